@@ -1,0 +1,206 @@
+/*
+ * bbc.h -- exact balanced-butterfly counting on one GB300 (sm_103a).
+ *
+ * The problem (Sec. III, "Problem Statement", of Mekala, Das, Banerjee and Ray,
+ * "Multi-core & GPU-based Balanced Butterfly Counting in Signed Bipartite Graphs",
+ * arXiv 2601.17707): given a signed bipartite graph G = (U, V, E+ u E-), count the
+ * butterflies (Def. 1: 4-cycles u-x-w-y with u, w in U and x, y in V) that hold an
+ * even number of negative edges (Def. 2, "balanced"). By Lemma 1 (Sec. IV) every
+ * pair {u, w} on one side with p symmetric and n asymmetric wedges (Defs. 7-9)
+ * closes C(p,2) + C(n,2) balanced and p*n unbalanced butterflies.
+ *
+ * Conventions of every call:
+ *   - Every call returns a bbc_status; nothing aborts or throws across this boundary.
+ *     bbc_last_error() gives a one-line description of the last failure on the
+ *     calling thread.
+ *   - Vertex ids are 0-based per side; signs are int8 +1 / -1 (Sec. III's "+" / "-").
+ *   - `cuda_stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream). Device work is queued on it; host outputs (pointers documented as
+ *     "host") are valid when the call returns, so those calls synchronise the stream.
+ *   - Inputs are copied; the caller keeps ownership of every buffer it passes.
+ *     A bbc_graph owns the device memory it allocates until bbc_graph_free.
+ *   - A bbc_graph is not thread-safe; a bbc_server is (submit / poll / wait).
+ */
+#ifndef BBC_H
+#define BBC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum bbc_status {
+    BBC_OK = 0,
+    BBC_E_INVALID_ARG = 1,     /* a NULL or negative argument, or inconsistent sizes */
+    BBC_E_OUT_OF_RANGE = 2,    /* an edge endpoint id outside [0, n_u) or [0, n_v) */
+    BBC_E_BAD_SIGN = 3,        /* a sign other than +1 or -1 */
+    BBC_E_DUPLICATE_EDGE = 4,  /* the same (u, v) pair twice, without BBC_DEDUP_LAST */
+    BBC_E_OVERFLOW_RISK = 5,   /* a count could exceed 2^64 - 1 */
+    BBC_E_NO_MEMORY = 6,       /* a device or host allocation failed */
+    BBC_E_OVER_BUDGET = 7,     /* a request larger than the server's device budget */
+    BBC_E_CUDA = 8,            /* a CUDA runtime error (see bbc_last_error) */
+    BBC_E_TIMEOUT = 9,         /* a bounded wait ran out */
+    BBC_E_CANCELLED = 10,      /* the server was shut down before the request finished */
+    BBC_E_NOT_READY = 11,      /* bbc_poll: the request is still in flight */
+    BBC_E_NO_DEVICE = 12       /* no usable CUDA device of compute capability 10.3 */
+} bbc_status;
+
+/* Flags of bbc_prepare. */
+enum {
+    BBC_INPUT_DEVICE = 1u,      /* u, v, sign are device pointers (default: host) */
+    BBC_DEDUP_LAST = 2u,        /* keep the last of repeated (u, v) pairs (Sec. VI keeps
+                                   the most recent rating) instead of failing */
+    BBC_SIDE_FORCE_U = 4u,      /* take U as the pair (anchor) side */
+    BBC_SIDE_FORCE_V = 8u,      /* take V as the pair (anchor) side */
+    BBC_ORIENT_LOW_ANCHOR = 16u /* count each pair at its lower-priority member (M-BBC's
+                                   p(w) < p(u) the other way round); same results */
+};
+
+typedef struct bbc_graph bbc_graph;
+typedef struct bbc_server bbc_server;
+
+/*
+ * Kernel tuning. Zero in any field selects the built-in default for it. The counts
+ * never depend on these values, only the speed does.
+ */
+typedef struct bbc_tuning {
+    int32_t tile_words;        /* endpoint counters per shared-memory tile (<= 53,248) */
+    int32_t warp_max_wedges;   /* anchors with at most this many oriented wedges go to the
+                                  one-warp hash path (<= 512) */
+    int32_t dense_min_permille;/* other anchors use dense tiles when wedges/span >= this/1000,
+                                  else the block hash path */
+    int32_t split_wedges;      /* anchors with more wedges than this are split into
+                                  tile-range items that run on different blocks */
+    int32_t blocks_per_sm;     /* resident blocks per SM of the tile kernel (1 or 2) */
+    int32_t reserved[3];
+} bbc_tuning;
+
+/* Fills *t with the built-in defaults. */
+bbc_status bbc_tuning_default(bbc_tuning *t);
+
+/*
+ * bbc_prepare -- validate the edge list and build the device layout the counting
+ * kernels read (Sec. IV "Vertex Priority", Def. 6; Algorithm 4's host preprocessing).
+ *
+ *   n_u, n_v    side sizes (>= 0); n_edges >= 0 edges given as u[i], v[i], sign[i].
+ *   u, v        int32 endpoint ids; sign: int8 +1 / -1. Host memory, or device memory
+ *               when BBC_INPUT_DEVICE is set. Not retained after the call.
+ *   flags       BBC_* flags above.
+ *   out         receives a new graph handle on success (untouched on failure).
+ *
+ * What it does: checks ids and signs (BBC_E_OUT_OF_RANGE / BBC_E_BAD_SIGN) and
+ * duplicate pairs (BBC_E_DUPLICATE_EDGE unless BBC_DEDUP_LAST); picks the pair side S
+ * as the side whose opposite side has the smaller sum of C(d, 2) (that sum is the
+ * number of oriented wedges W the count visits; ties pick U); ranks S and the centre
+ * side C by (degree descending, id descending) as in Def. 6; and builds two int32 CSR
+ * arrays with the sign in bit 31 of each column index: S -> C rows and C -> S rows,
+ * the latter sorted by rank so that the endpoints of higher rank form a suffix. It also
+ * estimates each anchor's wedge count and builds the work lists of bbc_count.
+ * Returns BBC_E_OVERFLOW_RISK when W * (max degree on S - 1) / 2 exceeds 2^64 - 1.
+ */
+bbc_status bbc_prepare(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_t *u,
+                       const int32_t *v, const int8_t *sign, uint32_t flags,
+                       void *cuda_stream, bbc_graph **out);
+
+/*
+ * bbc_count -- the exact counts of a prepared graph (Algorithms 2-4 of the paper
+ * compute `balanced`; the other outputs are extensions of this library).
+ *
+ *   balanced    host uint64: number of balanced butterflies (Def. 2). Required.
+ *   unbalanced  host uint64 or NULL: number of butterflies with an odd number of
+ *               negative edges.
+ *   per_u       device uint64[n_u] or NULL: per_u[x] = number of balanced butterflies
+ *               that contain vertex x of U. Overwritten.
+ *   per_v       device uint64[n_v] or NULL: the same for V.
+ *   tuning      NULL for the defaults.
+ * Synchronises `cuda_stream` before returning.
+ */
+bbc_status bbc_count(bbc_graph *g, uint64_t *balanced, uint64_t *unbalanced, uint64_t *per_u,
+                     uint64_t *per_v, const bbc_tuning *tuning, void *cuda_stream);
+
+/*
+ * bbc_count_async -- as bbc_count, but writes {balanced, unbalanced} into the device
+ * buffer totals_dev (2 x uint64, overwritten) and returns without synchronising.
+ * Every launch is queued on `cuda_stream`.
+ */
+bbc_status bbc_count_async(bbc_graph *g, uint64_t *totals_dev, uint64_t *per_u,
+                           uint64_t *per_v, const bbc_tuning *tuning, void *cuda_stream);
+
+/*
+ * bbc_graph_info -- facts about a prepared graph (any output pointer may be NULL).
+ *   side          0 when U is the pair side S, 1 when V is.
+ *   wedges        W, the number of oriented wedges bbc_count visits
+ *                 (sum over the centre side of C(d, 2)).
+ *   device_bytes  device memory the handle holds.
+ *   n_edges       edges after de-duplication.
+ */
+bbc_status bbc_graph_info(const bbc_graph *g, int32_t *side, uint64_t *wedges,
+                          size_t *device_bytes, int64_t *n_edges);
+
+/* Releases the handle and its device memory (NULL is a no-op). */
+void bbc_graph_free(bbc_graph *g);
+
+/*
+ * bbc_count_batch -- count n prepared graphs in one persistent launch over a device-side
+ * (graph, anchor) work list, captured once into a CUDA graph and replayed for later
+ * batches of the same graphs (the batched form of this library; the paper counts one
+ * graph at a time).
+ *   gs        n graph handles (each prepared on the device of the calling thread).
+ *   balanced  host uint64[n]: per-graph balanced counts. Required.
+ *   tuning    NULL: tuned choice (see bbc_autotune_batch), else the given values.
+ * Synchronises `cuda_stream`.
+ */
+bbc_status bbc_count_batch(int32_t n, bbc_graph *const *gs, uint64_t *balanced,
+                           const bbc_tuning *tuning, void *cuda_stream);
+
+/*
+ * bbc_autotune_batch -- times bbc_count_batch over a small grid of tile sizes, hash
+ * thresholds and split sizes on these graphs and stores the fastest in *best (and in
+ * the library's in-process cache, keyed by the batch's shape, which NULL-tuning batch
+ * calls then use). The counts are checked to agree across every candidate;
+ * a disagreement returns BBC_E_CUDA.
+ */
+bbc_status bbc_autotune_batch(int32_t n, bbc_graph *const *gs, bbc_tuning *best,
+                              void *cuda_stream);
+
+/*
+ * Serving loop: requests (edge lists in host memory) are copied, queued, admitted while
+ * the device memory they need fits the budget, prepared, and counted together with the
+ * other admitted requests in continuous batches on the server's own stream.
+ *   device_budget_bytes  upper bound of device memory held by admitted requests.
+ *   tuning               NULL for the defaults.
+ */
+bbc_status bbc_server_create(size_t device_budget_bytes, const bbc_tuning *tuning,
+                             bbc_server **out);
+
+/* Queues one request; its input is copied before the call returns. BBC_E_OVER_BUDGET
+ * when the request alone could never fit the budget. */
+bbc_status bbc_submit(bbc_server *s, int32_t n_u, int32_t n_v, int64_t n_edges,
+                      const int32_t *u, const int32_t *v, const int8_t *sign,
+                      uint64_t *ticket);
+
+/* BBC_OK with *balanced set when done, BBC_E_NOT_READY while in flight, or the
+ * request's own error status. A finished ticket may be polled again. */
+bbc_status bbc_poll(bbc_server *s, uint64_t ticket, uint64_t *balanced);
+
+/* Waits at most timeout_us microseconds (< 0: no limit) for a ticket. */
+bbc_status bbc_wait(bbc_server *s, uint64_t ticket, int64_t timeout_us, uint64_t *balanced);
+
+/* Latency statistics of finished requests, in microseconds from submit to completion. */
+bbc_status bbc_server_stats(bbc_server *s, uint64_t *completed, double *p50_us,
+                            double *p99_us, double *mean_us);
+
+/* Stops the loop; requests still queued finish with BBC_E_CANCELLED. */
+void bbc_server_destroy(bbc_server *s);
+
+/* Static strings; never NULL. */
+const char *bbc_status_string(bbc_status st);
+const char *bbc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BBC_H */

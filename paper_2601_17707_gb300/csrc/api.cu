@@ -1,0 +1,328 @@
+// api.cu -- the extern "C" entry points of include/bbc.h for single graphs, plus the
+// library's error state, memory pool and tuning defaults.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "graph.cuh"
+
+namespace bbc {
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+struct PoolEntry {
+    cudaMemPool_t pool = nullptr;
+    int sms = 0;
+};
+std::mutex g_pool_mu;
+PoolEntry g_pools[64];
+
+PoolEntry *device_entry() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    PoolEntry &e = g_pools[dev];
+    if (!e.pool) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        if (cudaMemPoolCreate(&e.pool, &props) != cudaSuccess) {
+            e.pool = nullptr;
+            return nullptr;
+        }
+        uint64_t keep = UINT64_MAX;  // keep freed blocks for reuse within this process
+        cudaMemPoolSetAttribute(e.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        cudaDeviceGetAttribute(&e.sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    return &e;
+}
+
+// The descriptor travels as a kernel argument, so queuing it never waits on the stream.
+__global__ void k_store_descriptor(DevGraph d, DevGraph *dst) { *dst = d; }
+
+__global__ void k_scatter_per_vertex(const unsigned long long *__restrict__ by_rank,
+                                     const int32_t *__restrict__ perm, int64_t n,
+                                     unsigned long long *__restrict__ out) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x)
+        out[perm[r]] = by_rank[r];
+}
+
+bbc_status check_device() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        set_error(std::string("no CUDA device: ") + cudaGetErrorString(e));
+        return BBC_E_NO_DEVICE;
+    }
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "device %d is sm_%d%d; this library is built for sm_103a", dev,
+                 major, minor);
+        set_error(buf);
+        return BBC_E_NO_DEVICE;
+    }
+    return BBC_OK;
+}
+
+}  // namespace
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+bbc_status cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return BBC_E_NO_MEMORY;
+    return BBC_E_CUDA;
+}
+
+bbc_status dev_alloc(void **p, size_t bytes, cudaStream_t st) {
+    PoolEntry *e = device_entry();
+    if (!e) {
+        set_error("could not create the device memory pool");
+        return BBC_E_CUDA;
+    }
+    cudaError_t err = cudaMallocFromPoolAsync(p, bytes, e->pool, st);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return cuda_fail(err, "cudaMallocFromPoolAsync");
+    }
+    return BBC_OK;
+}
+
+void dev_free(void *p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+
+int device_sm_count() {
+    PoolEntry *e = device_entry();
+    return e && e->sms > 0 ? e->sms : 148;
+}
+
+Tuning resolve_tuning(const bbc_tuning *t, int sm_count) {
+    (void)sm_count;
+    Tuning r;
+    r.tile_words = 26624;
+    r.warp_max_wedges = 256;
+    r.dense_min_permille = 0;
+    r.split_wedges = 0;  // 0: chosen per launch from the total work
+    r.blocks_per_sm = 2;
+    if (t) {
+        if (t->blocks_per_sm == 1 || t->blocks_per_sm == 2) r.blocks_per_sm = t->blocks_per_sm;
+        if (t->tile_words > 0) r.tile_words = t->tile_words;
+        if (t->warp_max_wedges > 0) r.warp_max_wedges = t->warp_max_wedges;
+        if (t->dense_min_permille > 0) r.dense_min_permille = t->dense_min_permille;
+        if (t->split_wedges > 0) r.split_wedges = t->split_wedges;
+    }
+    // limits: tiles are whole 16-byte groups and fit the per-block shared memory of the
+    // chosen residency; hash tables hold at most 512 wedges
+    const int cap = r.blocks_per_sm == 1 ? 53248 : 26624;
+    if (r.tile_words > cap) r.tile_words = cap;
+    if (r.tile_words < 1024) r.tile_words = 1024;
+    r.tile_words &= ~7;
+    if (r.warp_max_wedges > 512) r.warp_max_wedges = 512;
+    return r;
+}
+
+// Splits anchors whose wedge count exceeds a fair share of one block's work.
+long long auto_split(uint64_t wedges, int sm_count, int blocks_per_sm) {
+    const long long blocks = (long long)sm_count * blocks_per_sm;
+    long long s = (long long)(wedges / (uint64_t)(blocks * 4 > 0 ? blocks * 4 : 1));
+    if (s < (1ll << 22)) s = 1ll << 22;
+    return s;
+}
+
+bbc_status count_graph(bbc_graph *g, uint64_t *totals_dev, uint64_t *per_u, uint64_t *per_v,
+                       const bbc_tuning *tuning, cudaStream_t st) {
+    Tuning T = resolve_tuning(tuning, device_sm_count());
+    if (T.split_wedges == 0) T.split_wedges = auto_split(g->wedges, device_sm_count(), T.blocks_per_sm);
+    BBC_TRY(build_work_lists(g, T, st));
+    const bool pv = per_u || per_v;
+    if (pv && !g->bS) {
+        BBC_TRY(dev_alloc_n(&g->bS, (size_t)g->nS, st));
+        BBC_TRY(dev_alloc_n(&g->bC, (size_t)g->nC, st));
+        g->device_bytes += (size_t)(g->nS + g->nC) * 8;
+    }
+    if (pv) {
+        if (g->nS) BBC_CUDA_TRY(cudaMemsetAsync(g->bS, 0, (size_t)g->nS * 8, st));
+        if (g->nC) BBC_CUDA_TRY(cudaMemsetAsync(g->bC, 0, (size_t)g->nC * 8, st));
+    }
+    BBC_CUDA_TRY(cudaMemsetAsync(g->totals, 0, 16, st));
+    BBC_CUDA_TRY(cudaMemsetAsync(g->queue, 0, sizeof(QueueState), st));
+    static_assert(sizeof(DevGraph) % 8 == 0, "descriptor layout");
+    DevGraph d = host_descriptor(g, pv);
+    k_store_descriptor<<<1, 1, 0, st>>>(d, g->dgraph);
+    BBC_CUDA_TRY(cudaGetLastError());
+    CountLaunch L{};
+    L.graphs = g->dgraph;
+    L.tile_items = g->tile_pack;
+    L.n_tile_items = g->n_tile_pack;
+    L.wide_items = g->tile_wide;
+    L.n_wide_items = g->n_tile_wide;
+    L.warp_items = g->warp_items;
+    L.n_warp_items = g->n_warp;
+    L.queue = g->queue;
+    L.tuning = T;
+    BBC_TRY(launch_count(L, st));
+    if (pv) {
+        uint64_t *outS = g->side == 0 ? per_u : per_v;
+        uint64_t *outC = g->side == 0 ? per_v : per_u;
+        if (outS && g->nS) {
+            k_scatter_per_vertex<<<(unsigned)std::min<int64_t>((g->nS + 255) / 256, 4096), 256, 0, st>>>(
+                g->bS, g->permS, g->nS, reinterpret_cast<unsigned long long *>(outS));
+            BBC_CUDA_TRY(cudaGetLastError());
+        }
+        if (outC && g->nC) {
+            k_scatter_per_vertex<<<(unsigned)std::min<int64_t>((g->nC + 255) / 256, 4096), 256, 0, st>>>(
+                g->bC, g->permC, g->nC, reinterpret_cast<unsigned long long *>(outC));
+            BBC_CUDA_TRY(cudaGetLastError());
+        }
+    }
+    if (totals_dev && totals_dev != reinterpret_cast<uint64_t *>(g->totals))
+        BBC_CUDA_TRY(cudaMemcpyAsync(totals_dev, g->totals, 16, cudaMemcpyDeviceToDevice, st));
+    return BBC_OK;
+}
+
+}  // namespace bbc
+
+using namespace bbc;
+
+extern "C" {
+
+const char *bbc_status_string(bbc_status st) {
+    switch (st) {
+        case BBC_OK: return "ok";
+        case BBC_E_INVALID_ARG: return "invalid argument";
+        case BBC_E_OUT_OF_RANGE: return "vertex id out of range";
+        case BBC_E_BAD_SIGN: return "sign is not +1 or -1";
+        case BBC_E_DUPLICATE_EDGE: return "duplicate edge";
+        case BBC_E_OVERFLOW_RISK: return "count could overflow 64 bits";
+        case BBC_E_NO_MEMORY: return "out of memory";
+        case BBC_E_OVER_BUDGET: return "request exceeds the device memory budget";
+        case BBC_E_CUDA: return "CUDA error";
+        case BBC_E_TIMEOUT: return "timed out";
+        case BBC_E_CANCELLED: return "cancelled";
+        case BBC_E_NOT_READY: return "not ready";
+        case BBC_E_NO_DEVICE: return "no usable sm_103 device";
+    }
+    return "unknown status";
+}
+
+const char *bbc_last_error(void) { return bbc::g_last_error.c_str(); }
+
+bbc_status bbc_tuning_default(bbc_tuning *t) {
+    if (!t) return BBC_E_INVALID_ARG;
+    const Tuning r = resolve_tuning(nullptr, 0);
+    memset(t, 0, sizeof *t);
+    t->tile_words = r.tile_words;
+    t->warp_max_wedges = r.warp_max_wedges;
+    t->dense_min_permille = r.dense_min_permille;
+    t->split_wedges = 0;
+    t->blocks_per_sm = r.blocks_per_sm;
+    return BBC_OK;
+}
+
+bbc_status bbc_prepare(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_t *u,
+                       const int32_t *v, const int8_t *sign, uint32_t flags, void *cuda_stream,
+                       bbc_graph **out) {
+    try {
+        if (!out || n_u < 0 || n_v < 0 || n_edges < 0) {
+            set_error("bbc_prepare: NULL output or negative size");
+            return BBC_E_INVALID_ARG;
+        }
+        if (n_edges > 0 && (!u || !v || !sign)) {
+            set_error("bbc_prepare: NULL edge array");
+            return BBC_E_INVALID_ARG;
+        }
+        if ((flags & BBC_SIDE_FORCE_U) && (flags & BBC_SIDE_FORCE_V)) {
+            set_error("bbc_prepare: both side flags set");
+            return BBC_E_INVALID_ARG;
+        }
+        if (n_edges >= (int64_t)INT32_MAX || (int64_t)n_u + 1 >= (int64_t)INT32_MAX ||
+            (int64_t)n_v + 1 >= (int64_t)INT32_MAX) {
+            set_error("bbc_prepare: sizes must stay below 2^31 - 1");
+            return BBC_E_INVALID_ARG;
+        }
+        BBC_TRY(check_device());
+        return prepare_graph(n_u, n_v, n_edges, u, v, sign, flags,
+                             static_cast<cudaStream_t>(cuda_stream), out);
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return BBC_E_NO_MEMORY;
+    } catch (...) {
+        set_error("unexpected exception in bbc_prepare");
+        return BBC_E_CUDA;
+    }
+}
+
+bbc_status bbc_count_async(bbc_graph *g, uint64_t *totals_dev, uint64_t *per_u, uint64_t *per_v,
+                           const bbc_tuning *tuning, void *cuda_stream) {
+    if (!g) {
+        set_error("bbc_count_async: NULL graph");
+        return BBC_E_INVALID_ARG;
+    }
+    try {
+        return count_graph(g, totals_dev, per_u, per_v, tuning,
+                           static_cast<cudaStream_t>(cuda_stream));
+    } catch (...) {
+        set_error("unexpected exception in bbc_count_async");
+        return BBC_E_CUDA;
+    }
+}
+
+bbc_status bbc_count(bbc_graph *g, uint64_t *balanced, uint64_t *unbalanced, uint64_t *per_u,
+                     uint64_t *per_v, const bbc_tuning *tuning, void *cuda_stream) {
+    if (!g || !balanced) {
+        set_error("bbc_count: NULL graph or NULL balanced");
+        return BBC_E_INVALID_ARG;
+    }
+    try {
+        cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+        BBC_TRY(count_graph(g, nullptr, per_u, per_v, tuning, st));
+        unsigned long long host[2] = {0, 0};
+        QueueState q{};
+        BBC_CUDA_TRY(cudaMemcpyAsync(host, g->totals, 16, cudaMemcpyDeviceToHost, st));
+        BBC_CUDA_TRY(cudaMemcpyAsync(&q, g->queue, sizeof q, cudaMemcpyDeviceToHost, st));
+        BBC_CUDA_TRY(cudaStreamSynchronize(st));
+        if (q.error) {
+            set_error("counting kernel reported an internal inconsistency");
+            return BBC_E_CUDA;
+        }
+        *balanced = host[0];
+        if (unbalanced) *unbalanced = host[1];
+        return BBC_OK;
+    } catch (...) {
+        set_error("unexpected exception in bbc_count");
+        return BBC_E_CUDA;
+    }
+}
+
+bbc_status bbc_graph_info(const bbc_graph *g, int32_t *side, uint64_t *wedges,
+                          size_t *device_bytes, int64_t *n_edges) {
+    if (!g) return BBC_E_INVALID_ARG;
+    if (side) *side = g->side;
+    if (wedges) *wedges = g->wedges;
+    if (device_bytes) *device_bytes = g->device_bytes;
+    if (n_edges) *n_edges = g->n_edges;
+    return BBC_OK;
+}
+
+void bbc_graph_free(bbc_graph *g) {
+    if (!g) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != g->device) cudaSetDevice(g->device);
+    release_graph(g, nullptr);
+    cudaStreamSynchronize(nullptr);
+    if (prev != g->device) cudaSetDevice(prev);
+}
+
+}  // extern "C"

@@ -1,0 +1,432 @@
+// batch.cu -- bbc_count_batch / bbc_autotune_batch: many prepared graphs counted by one
+// persistent launch over a device-side (graph, anchor, tile range) work list.
+//
+// A "plan" concatenates the member graphs' work items (tagging each with its graph
+// index), re-orders all tile items by expected wedge count across graphs (largest
+// first), and records the memsets and counting launches into a CUDA graph once. Later
+// calls with the same graphs and tuning replay that graph: one launch of the whole
+// counting step, whatever the number of graphs.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "graph.cuh"
+
+namespace bbc {
+namespace {
+
+constexpr int kThreads = 256;
+
+struct CopyJob {
+    const void *src;
+    int64_t dst;
+    int32_t n;
+    int32_t graph;
+};
+
+template <class Item>
+__global__ void k_concat_items(const CopyJob *__restrict__ jobs, Item *__restrict__ dst) {
+    const CopyJob j = jobs[blockIdx.x];
+    const Item *src = static_cast<const Item *>(j.src);
+    for (int i = threadIdx.x; i < j.n; i += blockDim.x) {
+        Item it = src[i];
+        it.graph = j.graph;
+        dst[j.dst + i] = it;
+    }
+}
+
+// 16-bit key ordering tile items by expected wedges, largest first, across graphs.
+__global__ void k_tile_item_keys(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items,
+                                 int64_t n, int ept, uint32_t *__restrict__ keys,
+                                 uint32_t *__restrict__ order) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const TileItem it = items[i];
+        const DevGraph &G = graphs[it.graph];
+        const long long span = G.orient_low ? it.anchor : (long long)G.nS - 1 - it.anchor;
+        const long long nt = (span + ept - 1) / ept;
+        const double cost = (double)G.wl[it.anchor] * (double)(it.tile_end - it.tile_begin) /
+                                (double)(nt > 0 ? nt : 1) + 1.0;
+        int q = (int)(log2(cost) * 1024.0);
+        q = q < 0 ? 0 : (q > 65535 ? 65535 : q);
+        keys[i] = 65535u - (uint32_t)q;
+        order[i] = (uint32_t)i;
+    }
+}
+
+__global__ void k_gather_tile_items(const TileItem *__restrict__ in, const uint32_t *__restrict__ order,
+                                    int64_t n, TileItem *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[order[i]];
+}
+
+struct Plan {
+    std::vector<uint64_t> uids;
+    Tuning tuning{};
+    int device = 0;
+    int32_t n = 0;
+    DevGraph *dgraphs = nullptr;
+    unsigned long long *totals = nullptr;     // 2 per graph
+    unsigned long long *host_totals = nullptr;  // pinned
+    QueueState *queue = nullptr;
+    TileItem *pack = nullptr, *wide = nullptr;
+    HashItem *warp = nullptr;
+    int32_t n_pack = 0, n_wide = 0, n_warp = 0;
+    cudaStream_t stream = nullptr;            // capture / replay stream
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t exec = nullptr;
+
+    ~Plan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        void *ps[] = {dgraphs, totals, queue, pack, wide, warp};
+        for (void *p : ps)
+            if (p) dev_free(p, stream);
+        if (stream) cudaStreamSynchronize(stream);
+        if (host_totals) cudaFreeHost(host_totals);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        if (stream) cudaStreamDestroy(stream);
+    }
+};
+
+std::mutex g_plan_mu;
+std::vector<std::unique_ptr<Plan>> g_plans;  // most recent last; a handful kept
+constexpr size_t kMaxPlans = 4;
+
+std::mutex g_tune_mu;
+std::map<std::vector<long long>, Tuning> g_tuned;
+
+std::vector<long long> shape_key(int32_t n, bbc_graph *const *gs) {
+    long long e = 0, w = 0, s = 0;
+    for (int i = 0; i < n; ++i) {
+        e += gs[i]->n_edges;
+        w += (long long)gs[i]->wedges;
+        s += gs[i]->nS;
+    }
+    // coarse buckets (powers of two) so similar batches share a tuned choice
+    auto bucket = [](long long x) {
+        int b = 0;
+        while (x > 1) {
+            x >>= 1;
+            ++b;
+        }
+        return (long long)b;
+    };
+    return {n, bucket(e), bucket(w), bucket(s)};
+}
+
+bool same_tuning(const Tuning &a, const Tuning &b) {
+    return a.tile_words == b.tile_words && a.warp_max_wedges == b.warp_max_wedges &&
+           a.split_wedges == b.split_wedges && a.blocks_per_sm == b.blocks_per_sm;
+}
+
+#define BBC_LAUNCH_OK(what)                                        \
+    do {                                                           \
+        cudaError_t _e = cudaGetLastError();                       \
+        if (_e != cudaSuccess) return ::bbc::cuda_fail(_e, what);  \
+    } while (0)
+
+bbc_status build_plan(int32_t n, bbc_graph *const *gs, const Tuning &T, std::unique_ptr<Plan> &out) {
+    auto P = std::make_unique<Plan>();
+    P->n = n;
+    P->tuning = T;
+    cudaGetDevice(&P->device);
+    BBC_CUDA_TRY(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
+    BBC_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming));
+    BBC_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming));
+    cudaStream_t st = P->stream;
+    for (int i = 0; i < n; ++i) {
+        P->uids.push_back(gs[i]->uid);
+        if (gs[i]->device != P->device) {
+            set_error("bbc_count_batch: graphs prepared on another device");
+            return BBC_E_INVALID_ARG;
+        }
+        BBC_TRY(build_work_lists(gs[i], T, st));
+    }
+    std::vector<DevGraph> hd(n);
+    std::vector<CopyJob> jp, jw, jh;
+    int64_t np = 0, nw = 0, nh = 0;
+    BBC_TRY(dev_alloc_n(&P->totals, (size_t)2 * n, st));
+    for (int i = 0; i < n; ++i) {
+        bbc_graph *g = gs[i];
+        hd[i] = host_descriptor(g, false);
+        hd[i].totals = P->totals + 2 * i;
+        if (g->n_tile_pack) jp.push_back(CopyJob{g->tile_pack, np, g->n_tile_pack, i});
+        if (g->n_tile_wide) jw.push_back(CopyJob{g->tile_wide, nw, g->n_tile_wide, i});
+        if (g->n_warp) jh.push_back(CopyJob{g->warp_items, nh, g->n_warp, i});
+        np += g->n_tile_pack;
+        nw += g->n_tile_wide;
+        nh += g->n_warp;
+    }
+    if (np > INT32_MAX || nw > INT32_MAX || nh > INT32_MAX) {
+        set_error("bbc_count_batch: too many work items");
+        return BBC_E_INVALID_ARG;
+    }
+    P->n_pack = (int32_t)np;
+    P->n_wide = (int32_t)nw;
+    P->n_warp = (int32_t)nh;
+    BBC_TRY(dev_alloc_n(&P->dgraphs, (size_t)n, st));
+    BBC_TRY(dev_alloc_n(&P->queue, 1, st));
+    BBC_TRY(dev_alloc_n(&P->pack, (size_t)np, st));
+    BBC_TRY(dev_alloc_n(&P->wide, (size_t)nw, st));
+    BBC_TRY(dev_alloc_n(&P->warp, (size_t)nh, st));
+    BBC_CUDA_TRY(cudaMallocHost(&P->host_totals, sizeof(unsigned long long) * 2 * (size_t)std::max(n, 1)));
+    BBC_CUDA_TRY(cudaMemcpyAsync(P->dgraphs, hd.data(), sizeof(DevGraph) * (size_t)n,
+                                 cudaMemcpyHostToDevice, st));
+    // concatenate, tagging each item with its graph index
+    CopyJob *djobs = nullptr;
+    const size_t maxj = std::max(jp.size(), std::max(jw.size(), jh.size()));
+    BBC_TRY(dev_alloc_n(&djobs, maxj, st));
+    struct Part {
+        std::vector<CopyJob> *jobs;
+        int which;
+    } parts[3] = {{&jp, 0}, {&jw, 1}, {&jh, 2}};
+    bbc_status s = BBC_OK;
+    for (auto &pt : parts) {
+        if (pt.jobs->empty()) continue;
+        cudaError_t e = cudaMemcpyAsync(djobs, pt.jobs->data(), sizeof(CopyJob) * pt.jobs->size(),
+                                        cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+            s = cuda_fail(e, "batch job copy");
+            break;
+        }
+        const unsigned nb = (unsigned)pt.jobs->size();
+        if (pt.which == 0) k_concat_items<TileItem><<<nb, kThreads, 0, st>>>(djobs, P->pack);
+        if (pt.which == 1) k_concat_items<TileItem><<<nb, kThreads, 0, st>>>(djobs, P->wide);
+        if (pt.which == 2) k_concat_items<HashItem><<<nb, kThreads, 0, st>>>(djobs, P->warp);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // djobs is reused
+        if (e != cudaSuccess) {
+            s = cuda_fail(e, "k_concat_items");
+            break;
+        }
+    }
+    dev_free(djobs, st);
+    BBC_TRY(s);
+    // order tile items across graphs, heaviest first
+    for (int which = 0; which < 2; ++which) {
+        const int64_t cnt = which == 0 ? np : nw;
+        if (cnt <= 1) continue;
+        TileItem *items = which == 0 ? P->pack : P->wide;
+        const int ept = which == 0 ? T.tile_words : T.tile_words / 2;
+        uint32_t *keys = nullptr, *order = nullptr;
+        TileItem *sorted = nullptr;
+        BBC_TRY(dev_alloc_n(&keys, (size_t)cnt, st));
+        BBC_TRY(dev_alloc_n(&order, (size_t)cnt, st));
+        BBC_TRY(dev_alloc_n(&sorted, (size_t)cnt, st));
+        const unsigned grid = (unsigned)std::min<int64_t>((cnt + kThreads - 1) / kThreads, 4096);
+        k_tile_item_keys<<<grid, kThreads, 0, st>>>(P->dgraphs, items, cnt, ept, keys, order);
+        BBC_LAUNCH_OK("k_tile_item_keys");
+        BBC_TRY(radix_sort_pairs(keys, order, cnt, 16, st));
+        k_gather_tile_items<<<grid, kThreads, 0, st>>>(items, order, cnt, sorted);
+        BBC_LAUNCH_OK("k_gather_tile_items");
+        dev_free(keys, st);
+        dev_free(order, st);
+        dev_free(items, st);
+        if (which == 0)
+            P->pack = sorted;
+        else
+            P->wide = sorted;
+    }
+    BBC_CUDA_TRY(cudaStreamSynchronize(st));
+    // record the counting step once
+    BBC_TRY(configure_count_kernels());
+    CountLaunch L{};
+    L.graphs = P->dgraphs;
+    L.tile_items = P->pack;
+    L.n_tile_items = P->n_pack;
+    L.wide_items = P->wide;
+    L.n_wide_items = P->n_wide;
+    L.warp_items = P->warp;
+    L.n_warp_items = P->n_warp;
+    L.queue = P->queue;
+    L.tuning = T;
+    BBC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaMemsetAsync(P->totals, 0, sizeof(unsigned long long) * 2 * (size_t)n, st);
+    cudaMemsetAsync(P->queue, 0, sizeof(QueueState), st);
+    bbc_status ls = launch_count(L, st);
+    cudaMemcpyAsync(P->host_totals, P->totals, sizeof(unsigned long long) * 2 * (size_t)n,
+                    cudaMemcpyDeviceToHost, st);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    BBC_TRY(ls);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&P->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    out = std::move(P);
+    return BBC_OK;
+}
+
+Plan *find_or_build(int32_t n, bbc_graph *const *gs, const Tuning &T, bbc_status *status) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (size_t k = 0; k < g_plans.size(); ++k) {
+        Plan *p = g_plans[k].get();
+        if (p->n != n || p->device != dev || !same_tuning(p->tuning, T)) continue;
+        bool same = true;
+        for (int i = 0; i < n && same; ++i) same = p->uids[i] == gs[i]->uid;
+        if (same) {
+            auto keep = std::move(g_plans[k]);
+            g_plans.erase(g_plans.begin() + (long)k);
+            g_plans.push_back(std::move(keep));
+            *status = BBC_OK;
+            return g_plans.back().get();
+        }
+    }
+    std::unique_ptr<Plan> p;
+    *status = build_plan(n, gs, T, p);
+    if (*status != BBC_OK) return nullptr;
+    g_plans.push_back(std::move(p));
+    while (g_plans.size() > kMaxPlans) g_plans.erase(g_plans.begin());
+    return g_plans.back().get();
+}
+
+// Replays a plan ordered after `st` and waits for it; fills balanced[] (and the
+// elapsed device time in ms when `ms` is given).
+bbc_status run_plan(Plan *p, uint64_t *balanced, cudaStream_t st, float *ms) {
+    BBC_CUDA_TRY(cudaEventRecord(p->ev_in, st));
+    BBC_CUDA_TRY(cudaStreamWaitEvent(p->stream, p->ev_in, 0));
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (ms) {
+        BBC_CUDA_TRY(cudaEventCreate(&t0));
+        BBC_CUDA_TRY(cudaEventCreate(&t1));
+        BBC_CUDA_TRY(cudaEventRecord(t0, p->stream));
+    }
+    BBC_CUDA_TRY(cudaGraphLaunch(p->exec, p->stream));
+    if (ms) BBC_CUDA_TRY(cudaEventRecord(t1, p->stream));
+    BBC_CUDA_TRY(cudaEventRecord(p->ev_out, p->stream));
+    BBC_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_out, 0));
+    BBC_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    if (ms) {
+        cudaEventElapsedTime(ms, t0, t1);
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+    }
+    if (balanced)
+        for (int i = 0; i < p->n; ++i) balanced[i] = p->host_totals[2 * i];
+    return BBC_OK;
+}
+
+bbc_status check_graphs(int32_t n, bbc_graph *const *gs) {
+    if (n < 0 || (n > 0 && !gs)) {
+        set_error("bbc_count_batch: bad graph list");
+        return BBC_E_INVALID_ARG;
+    }
+    for (int i = 0; i < n; ++i)
+        if (!gs[i]) {
+            set_error("bbc_count_batch: NULL graph in the list");
+            return BBC_E_INVALID_ARG;
+        }
+    return BBC_OK;
+}
+
+Tuning batch_tuning(int32_t n, bbc_graph *const *gs, const bbc_tuning *t) {
+    Tuning T = resolve_tuning(t, device_sm_count());
+    if (!t) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(shape_key(n, gs));
+        if (it != g_tuned.end()) T = it->second;
+    }
+    if (T.split_wedges == 0) {
+        uint64_t w = 0;
+        for (int i = 0; i < n; ++i) w += gs[i]->wedges;
+        T.split_wedges = auto_split(w, device_sm_count(), T.blocks_per_sm);
+    }
+    return T;
+}
+
+}  // namespace
+
+bbc_status count_batch_impl(int32_t n, bbc_graph *const *gs, uint64_t *balanced,
+                            const bbc_tuning *tuning, cudaStream_t st, float *ms) {
+    BBC_TRY(check_graphs(n, gs));
+    if (n == 0) return BBC_OK;
+    const Tuning T = batch_tuning(n, gs, tuning);
+    bbc_status s = BBC_OK;
+    Plan *p = find_or_build(n, gs, T, &s);
+    if (!p) return s;
+    return run_plan(p, balanced, st, ms);
+}
+
+}  // namespace bbc
+
+using namespace bbc;
+
+extern "C" {
+
+bbc_status bbc_count_batch(int32_t n, bbc_graph *const *gs, uint64_t *balanced,
+                           const bbc_tuning *tuning, void *cuda_stream) {
+    if (!balanced && n > 0) {
+        set_error("bbc_count_batch: NULL output");
+        return BBC_E_INVALID_ARG;
+    }
+    try {
+        return count_batch_impl(n, gs, balanced, tuning, static_cast<cudaStream_t>(cuda_stream),
+                                nullptr);
+    } catch (...) {
+        set_error("unexpected exception in bbc_count_batch");
+        return BBC_E_CUDA;
+    }
+}
+
+bbc_status bbc_autotune_batch(int32_t n, bbc_graph *const *gs, bbc_tuning *best,
+                              void *cuda_stream) {
+    if (!best) return BBC_E_INVALID_ARG;
+    try {
+        BBC_TRY(check_graphs(n, gs));
+        cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+        struct Cand {
+            int tile_words, blocks_per_sm, warp_max;
+        };
+        const Cand cands[] = {
+            {26624, 2, 256}, {26624, 2, 64}, {26624, 2, 512}, {16384, 2, 256},
+            {8192, 2, 256},  {53248, 1, 256}, {8192, 2, 512},  {4096, 2, 512},
+        };
+        std::vector<uint64_t> ref(std::max(n, 1)), got(std::max(n, 1));
+        bool have_ref = false;
+        float best_ms = 1e30f;
+        bbc_tuning best_t{};
+        for (const Cand &c : cands) {
+            bbc_tuning t{};
+            t.tile_words = c.tile_words;
+            t.blocks_per_sm = c.blocks_per_sm;
+            t.warp_max_wedges = c.warp_max;
+            float ms_best = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                float ms = 0.f;
+                BBC_TRY(count_batch_impl(n, gs, got.data(), &t, st, &ms));
+                if (rep > 0) ms_best = std::min(ms_best, ms);
+            }
+            if (!have_ref) {
+                ref = got;
+                have_ref = true;
+            } else if (ref != got) {
+                set_error("bbc_autotune_batch: candidates disagree on the counts");
+                return BBC_E_CUDA;
+            }
+            if (ms_best < best_ms) {
+                best_ms = ms_best;
+                best_t = t;
+            }
+        }
+        *best = best_t;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tuned[shape_key(n, gs)] = resolve_tuning(&best_t, device_sm_count());
+        }
+        return BBC_OK;
+    } catch (...) {
+        set_error("unexpected exception in bbc_autotune_batch");
+        return BBC_E_CUDA;
+    }
+}
+
+}  // extern "C"

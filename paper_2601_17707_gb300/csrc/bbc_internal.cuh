@@ -1,0 +1,144 @@
+// bbc_internal.cuh -- device layout, work items and launchers shared by the library's
+// translation units. Not part of the public boundary (include/bbc.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/bbc.h"
+
+namespace bbc {
+
+constexpr uint32_t kSignBit = 0x80000000u;
+constexpr uint32_t kIdMask = 0x7fffffffu;
+
+// One prepared graph as the counting kernels see it. S is the pair (anchor/endpoint)
+// side, C the centre side; both are relabelled by rank (degree descending, id
+// descending, Def. 6). Entries pack the neighbour's rank with the edge sign in bit 31
+// (set = negative edge).
+struct DevGraph {
+    const int64_t *rowS_off;   // nS + 1
+    const uint32_t *rowS;      // S -> C entries (centre rank | sign)
+    const int64_t *rowC_off;   // nC + 1
+    const uint32_t *rowC;      // C -> S entries (anchor rank | sign), ascending rank per row
+    int32_t nS, nC;
+    int32_t orient_low;        // 0: anchor a pairs with endpoints of higher rank (lower
+                               // priority); 1: with endpoints of lower rank
+    int32_t pad;
+    unsigned long long *bS;    // per-vertex balanced counts by S rank (nullable)
+    unsigned long long *bC;    // per-vertex balanced counts by C rank (nullable)
+    unsigned long long *totals;// [0] balanced, [1] unbalanced
+    const unsigned long long *wl; // oriented wedges per anchor rank (orders work items)
+};
+
+// A unit of work of the tile kernel: anchor `anchor` of graph `graph`, endpoint tiles
+// [tile_begin, tile_end) of width `tile_words` over the anchor's endpoint range.
+struct TileItem {
+    int32_t graph;
+    int32_t anchor;
+    int32_t tile_begin;
+    int32_t tile_end;
+};
+
+// A unit of work of the hash kernel: one anchor and its oriented wedge count.
+struct HashItem {
+    int32_t graph;
+    int32_t anchor;
+    int32_t wedges;
+    int32_t pad;
+};
+
+// Queue heads and the error word of the persistent kernels; zeroed before a launch.
+struct QueueState {
+    unsigned int tile_head;    // packed-counter tile items
+    unsigned int wide_head;    // 32-bit-counter tile items
+    unsigned int warp_head;    // hash items
+    unsigned int error;        // nonzero: a kernel saw an impossible state (see kErr*)
+};
+
+enum : unsigned int {
+    kErrHashFull = 1u,         // a hash table ran out of slots (work estimate was wrong)
+    kErrBadItem = 2u,
+};
+
+struct Tuning {
+    int tile_words;
+    int warp_max_wedges;
+    int dense_min_permille;
+    long long split_wedges;
+    int blocks_per_sm;
+};
+
+Tuning resolve_tuning(const bbc_tuning *t, int sm_count);
+
+// ----------------------------------------------------------------------------- errors
+
+void set_error(const std::string &msg);
+bbc_status cuda_fail(cudaError_t e, const char *what);
+
+#define BBC_CUDA_TRY(expr)                                                    \
+    do {                                                                      \
+        cudaError_t _e = (expr);                                              \
+        if (_e != cudaSuccess) return ::bbc::cuda_fail(_e, #expr);            \
+    } while (0)
+
+#define BBC_TRY(expr)                                                         \
+    do {                                                                      \
+        bbc_status _s = (expr);                                               \
+        if (_s != BBC_OK) return _s;                                          \
+    } while (0)
+
+// ----------------------------------------------------------------------------- memory
+
+// Stream-ordered allocation from the library's own pool on the current device.
+bbc_status dev_alloc(void **p, size_t bytes, cudaStream_t st);
+void dev_free(void *p, cudaStream_t st);
+
+template <class T>
+bbc_status dev_alloc_n(T **p, size_t n, cudaStream_t st) {
+    return dev_alloc(reinterpret_cast<void **>(p), n * sizeof(T) + (n == 0 ? 16 : 0), st);
+}
+
+int device_sm_count();
+
+// ----------------------------------------------------------------------------- sort/scan
+
+// Stable LSD radix sort of (key, value) pairs by the low `bits` bits of the key.
+// keys/vals are sorted in place (scratch buffers are allocated from the pool).
+bbc_status radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, int bits,
+                            cudaStream_t st);
+
+// out[i] = sum_{j < i} in[j] for i in [0, n]; out has n + 1 entries.
+bbc_status exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n,
+                                     cudaStream_t st);
+bbc_status exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t st);
+
+// ----------------------------------------------------------------------------- counting
+
+struct CountLaunch {
+    const DevGraph *graphs;     // device array
+    const TileItem *tile_items; // device, packed 16-bit counters
+    int32_t n_tile_items;
+    const TileItem *wide_items; // device, 32-bit counters
+    int32_t n_wide_items;
+    const HashItem *warp_items; // device
+    int32_t n_warp_items;
+    QueueState *queue;          // device, zeroed by the caller before the launch
+    Tuning tuning;
+};
+
+// Queues the counting kernels (packed tiles, wide tiles, warp hash) on `st`.
+bbc_status launch_count(const CountLaunch &L, cudaStream_t st);
+
+// Sets the kernels' shared-memory limits on the current device (idempotent); done
+// before any stream capture so that capture only records launches.
+bbc_status configure_count_kernels();
+
+int tile_kernel_smem_bytes(int tile_words, bool wide);
+
+// Splits anchors whose wedge count exceeds a fair share of one block's work.
+long long auto_split(uint64_t wedges, int sm_count, int blocks_per_sm);
+
+}  // namespace bbc

@@ -1,0 +1,56 @@
+// graph.cuh -- the host-side handle of a prepared graph (the opaque bbc_graph of bbc.h).
+#pragma once
+
+#include "bbc_internal.cuh"
+
+struct bbc_graph {
+    uint64_t uid = 0;          // unique per handle within the process (never reused)
+    int device = 0;
+    int32_t n_u = 0, n_v = 0;
+    int64_t n_edges = 0;       // after de-duplication
+    int side = 0;              // 0: S = U (pairs on U, centres on V); 1: S = V
+    int side_paper_rule = 0;   // the paper's choice S = min(|U|, |V|) (Alg. 2-4), for reports
+    int orient_low = 0;
+    int32_t nS = 0, nC = 0;
+    uint64_t wedges = 0;       // W = sum over C of C(d, 2)
+    int32_t max_deg_S = 0, max_deg_C = 0;
+
+    // device layout (owned)
+    int64_t *rowS_off = nullptr;
+    uint32_t *rowS = nullptr;
+    int64_t *rowC_off = nullptr;
+    uint32_t *rowC = nullptr;
+    int32_t *permS = nullptr;  // rank -> original id
+    int32_t *permC = nullptr;
+    unsigned long long *wl = nullptr;  // oriented wedges per anchor rank
+
+    // work lists (rebuilt when the tuning changes)
+    bbc::Tuning items_tuning{};
+    bool items_valid = false;
+    bbc::TileItem *tile_pack = nullptr;
+    int32_t n_tile_pack = 0;
+    bbc::TileItem *tile_wide = nullptr;
+    int32_t n_tile_wide = 0;
+    bbc::HashItem *warp_items = nullptr;
+    int32_t n_warp = 0;
+
+    // count-time state
+    bbc::DevGraph *dgraph = nullptr;       // device copy of the descriptor
+    unsigned long long *bS = nullptr;      // per-vertex by rank, allocated on first use
+    unsigned long long *bC = nullptr;
+    unsigned long long *totals = nullptr;  // 2 words
+    bbc::QueueState *queue = nullptr;
+
+    size_t device_bytes = 0;
+};
+
+namespace bbc {
+
+bbc_status prepare_graph(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_t *u,
+                         const int32_t *v, const int8_t *sign, uint32_t flags, cudaStream_t st,
+                         bbc_graph **out);
+bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st);
+void release_graph(bbc_graph *g, cudaStream_t st);
+DevGraph host_descriptor(const bbc_graph *g, bool per_vertex);
+
+}  // namespace bbc

@@ -1,0 +1,660 @@
+// prep.cu -- graph preparation on the device (bbc_prepare).
+//
+// Steps, all in this file's kernels plus the radix sort / scan of sort_scan.cu:
+//   1. validate ids and signs, count degrees (k_validate_degrees);
+//   2. per side sum of C(d, 2) and max degree (k_degree_stats) -> the pair side S is
+//      the side whose opposite side has the smaller sum (that sum is W, the number of
+//      oriented wedges the count visits);
+//   3. rank S and C by (degree descending, id descending), the vertex priority of
+//      Def. 6 (k_rank_keys + stable radix sort + k_invert_perm);
+//   4. map every edge to (rank_S, rank_C | sign << 31) and sort it twice, stably:
+//      by rank_S (giving the S -> C rows) and then by rank_C (giving the C -> S rows,
+//      each sorted by anchor rank because the input of the second sort is already in
+//      rank_S order); duplicates are adjacent there (k_count_duplicates);
+//   5. row offsets by exclusive scans of the ranked degrees;
+//   6. per anchor the number of oriented wedges it visits (k_wedge_estimate), then the
+//      work lists (k_classify + k_emit_items + a cost-ordered radix sort), heavy first
+//      as in the fanout ordering of Algorithm 4.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+
+#include "graph.cuh"
+
+namespace bbc {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(int64_t n, int threads = kThreads) {
+    int64_t b = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)device_sm_count() * 32;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+inline int bit_length(uint64_t x) {
+    int b = 0;
+    while (x) {
+        ++b;
+        x >>= 1;
+    }
+    return b;
+}
+
+__global__ void k_validate_degrees(const int32_t *__restrict__ u, const int32_t *__restrict__ v,
+                                   const int8_t *__restrict__ s, int64_t n, int32_t n_u,
+                                   int32_t n_v, int32_t *__restrict__ deg_u,
+                                   int32_t *__restrict__ deg_v, unsigned *__restrict__ err) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = u[i], b = v[i];
+        const int8_t sg = s[i];
+        unsigned bad = 0;
+        if (a < 0 || a >= n_u || b < 0 || b >= n_v) bad |= 1u;
+        if (sg != 1 && sg != -1) bad |= 2u;
+        if (bad) {
+            atomicOr(err, bad);
+            continue;
+        }
+        atomicAdd(deg_u + a, 1);
+        atomicAdd(deg_v + b, 1);
+    }
+}
+
+// stats[0] += sum C(d, 2) (uint64), stats[1] = max d (as uint64 via atomicMax)
+__global__ void k_degree_stats(const int32_t *__restrict__ deg, int64_t n,
+                               unsigned long long *__restrict__ stats) {
+    unsigned long long s = 0, m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long d = (unsigned long long)deg[i];
+        s += d * (d - (d > 0)) / 2;
+        m = d > m ? d : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_down_sync(kFull, s, o);
+        const unsigned long long mo = __shfl_down_sync(kFull, m, o);
+        m = mo > m ? mo : m;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(stats + 0, s);
+        atomicMax(stats + 1, m);
+    }
+}
+
+// keys[i] = maxdeg - deg[id], vals[i] = id, with id = n - 1 - i: a stable ascending sort
+// then lists ids by degree descending and, among equal degrees, id descending.
+__global__ void k_rank_keys(const int32_t *__restrict__ deg, int64_t n, int32_t maxdeg,
+                            uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t id = n - 1 - i;
+        keys[i] = (uint32_t)(maxdeg - deg[id]);
+        vals[i] = (uint32_t)id;
+    }
+}
+
+__global__ void k_invert_perm(const uint32_t *__restrict__ perm, int64_t n,
+                              int32_t *__restrict__ rank, int32_t *__restrict__ perm_out) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t id = perm[r];
+        rank[id] = (int32_t)r;
+        perm_out[r] = (int32_t)id;
+    }
+}
+
+__global__ void k_gather_deg(const int32_t *__restrict__ deg, const int32_t *__restrict__ perm,
+                             int64_t n, int32_t *__restrict__ out) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x)
+        out[r] = deg[perm[r]];
+}
+
+__global__ void k_map_edges(const int32_t *__restrict__ u, const int32_t *__restrict__ v,
+                            const int8_t *__restrict__ s, int64_t n, int side,
+                            const int32_t *__restrict__ rankS, const int32_t *__restrict__ rankC,
+                            uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t sid = side == 0 ? u[i] : v[i];
+        const int32_t cid = side == 0 ? v[i] : u[i];
+        keys[i] = (uint32_t)rankS[sid];
+        vals[i] = (uint32_t)rankC[cid] | (s[i] < 0 ? kSignBit : 0u);
+    }
+}
+
+// (rank_S, rank_C | sign) -> (rank_C, rank_S | sign)
+__global__ void k_swap_sides(const uint32_t *__restrict__ ka, const uint32_t *__restrict__ va,
+                             int64_t n, uint32_t *__restrict__ kb, uint32_t *__restrict__ vb) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = va[i];
+        kb[i] = x & kIdMask;
+        vb[i] = ka[i] | (x & kSignBit);
+    }
+}
+
+__global__ void k_count_duplicates(const uint32_t *__restrict__ kc, const uint32_t *__restrict__ vc,
+                                   int64_t n, unsigned long long *__restrict__ dups) {
+    unsigned long long c = 0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        if (kc[j] == kc[j - 1] && ((vc[j] ^ vc[j - 1]) & kIdMask) == 0) ++c;
+    }
+    if (c) atomicAdd(dups, c);
+}
+
+// Keeps the last entry of every run of equal (rank_C, rank_S) -- the last occurrence in
+// input order, since both sorts are stable -- and writes it back as an original-id edge.
+__global__ void k_dedup_last(const uint32_t *__restrict__ kc, const uint32_t *__restrict__ vc,
+                             int64_t n, const int64_t *__restrict__ pos, int side,
+                             const int32_t *__restrict__ permS, const int32_t *__restrict__ permC,
+                             int32_t *__restrict__ u, int32_t *__restrict__ v,
+                             int8_t *__restrict__ s) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const bool last = j == n - 1 || kc[j + 1] != kc[j] || ((vc[j + 1] ^ vc[j]) & kIdMask) != 0;
+        if (!last) continue;
+        const int64_t o = pos[j];
+        const int32_t cid = permC[kc[j]];
+        const int32_t sid = permS[vc[j] & kIdMask];
+        u[o] = side == 0 ? sid : cid;
+        v[o] = side == 0 ? cid : sid;
+        s[o] = (vc[j] & kSignBit) ? (int8_t)-1 : (int8_t)1;
+    }
+}
+
+__global__ void k_last_flags(const uint32_t *__restrict__ kc, const uint32_t *__restrict__ vc,
+                             int64_t n, int32_t *__restrict__ flag) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x)
+        flag[j] = (j == n - 1 || kc[j + 1] != kc[j] || ((vc[j + 1] ^ vc[j]) & kIdMask) != 0) ? 1 : 0;
+}
+
+__device__ __forceinline__ int64_t lower_bound_rank(const uint32_t *__restrict__ row, int64_t b,
+                                                    int64_t e, uint32_t key) {
+    while (b < e) {
+        const int64_t m = (b + e) >> 1;
+        if ((__ldg(row + m) & kIdMask) < key)
+            b = m + 1;
+        else
+            e = m;
+    }
+    return b;
+}
+
+// wl[a] = number of oriented wedges at anchor a: for every entry (a, c) of the S -> C
+// rows, the entries of row c of higher (orient_low: lower) rank than a. The rows are
+// grouped by anchor, so a segmented warp sum leaves one atomic per anchor run.
+__global__ void k_wedge_estimate(const uint32_t *__restrict__ anchor_of, const uint32_t *__restrict__ rowS,
+                                 int64_t n, const int64_t *__restrict__ rowC_off,
+                                 const uint32_t *__restrict__ rowC, int orient_low,
+                                 unsigned long long *__restrict__ wl) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t e = base + threadIdx.x;
+        const bool valid = e < n;
+        uint32_t a = 0xffffffffu;
+        unsigned long long cnt = 0;
+        if (valid) {
+            a = anchor_of[e];
+            const uint32_t c = rowS[e] & kIdMask;
+            const int64_t b = rowC_off[c], en = rowC_off[c + 1];
+            const int64_t p = lower_bound_rank(rowC, b, en, a);
+            cnt = orient_low ? (unsigned long long)(p - b) : (unsigned long long)(en - p - 1);
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, cnt, o);
+            const uint32_t ka = __shfl_up_sync(kFull, a, o);
+            if (lane >= o && ka == a) cnt += y;
+        }
+        const uint32_t next = __shfl_down_sync(kFull, a, 1);
+        if (valid && (lane == 31 || next != a) && cnt) atomicAdd(wl + a, cnt);
+    }
+}
+
+struct ClassifyParams {
+    int32_t nS;
+    int orient_low;
+    int tile_words;
+    int warp_max;
+    long long split;
+};
+
+__device__ __forceinline__ void classify_one(const ClassifyParams &P, unsigned long long wl,
+                                             int64_t deg, int a, int *kind, int *ntiles,
+                                             int *groups) {
+    *kind = 0;
+    *ntiles = 0;
+    *groups = 0;
+    if (wl == 0 || deg < 2) return;
+    if ((long long)wl <= P.warp_max) {
+        *kind = 1;
+        return;
+    }
+    const long long maxcount = deg < (long long)wl ? deg : (long long)wl;
+    const bool wide = maxcount > 65535;
+    const int ept = wide ? P.tile_words / 2 : P.tile_words;
+    const long long span = P.orient_low ? a : (long long)P.nS - 1 - a;
+    const int nt = (int)((span + ept - 1) / ept);
+    long long g = 1;
+    if ((long long)wl > P.split) g = ((long long)wl + P.split - 1) / P.split;
+    if (g > nt) g = nt;
+    *kind = wide ? 3 : 2;
+    *ntiles = nt;
+    *groups = (int)g;
+}
+
+// Per anchor: how many packed-tile items, wide-tile items and warp items it yields.
+__global__ void k_classify(ClassifyParams P, const unsigned long long *__restrict__ wl,
+                           const int64_t *__restrict__ rowS_off, int32_t *__restrict__ n_pack,
+                           int32_t *__restrict__ n_wide, int32_t *__restrict__ n_warp) {
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < P.nS;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        int kind, nt, g;
+        classify_one(P, wl[a], rowS_off[a + 1] - rowS_off[a], (int)a, &kind, &nt, &g);
+        n_pack[a] = kind == 2 ? g : 0;
+        n_wide[a] = kind == 3 ? g : 0;
+        n_warp[a] = kind == 1 ? 1 : 0;
+    }
+}
+
+// Writes the items and, per tile item, a 16-bit sort key that orders items by their
+// expected wedge count, largest first (the fanout ordering of Algorithm 4).
+__global__ void k_emit_items(ClassifyParams P, const unsigned long long *__restrict__ wl,
+                             const int64_t *__restrict__ rowS_off, const int64_t *__restrict__ pos_pack,
+                             const int64_t *__restrict__ pos_wide, const int64_t *__restrict__ pos_warp,
+                             TileItem *__restrict__ pack, uint32_t *__restrict__ key_pack,
+                             TileItem *__restrict__ wide, uint32_t *__restrict__ key_wide,
+                             HashItem *__restrict__ warp) {
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < P.nS;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        int kind, nt, g;
+        const unsigned long long w = wl[a];
+        classify_one(P, w, rowS_off[a + 1] - rowS_off[a], (int)a, &kind, &nt, &g);
+        if (kind == 1) {
+            warp[pos_warp[a]] = HashItem{0, (int32_t)a, (int32_t)w, 0};
+        } else if (kind >= 2) {
+            TileItem *dst = kind == 2 ? pack + pos_pack[a] : wide + pos_wide[a];
+            uint32_t *kd = kind == 2 ? key_pack + pos_pack[a] : key_wide + pos_wide[a];
+            for (int i = 0; i < g; ++i) {
+                const int t0 = (int)((long long)nt * i / g);
+                const int t1 = (int)((long long)nt * (i + 1) / g);
+                dst[i] = TileItem{0, (int32_t)a, t0, t1};
+                const double cost = (double)w * (double)(t1 - t0) / (double)nt + 1.0;
+                int q = (int)(log2(cost) * 1024.0);
+                q = q < 0 ? 0 : (q > 65535 ? 65535 : q);
+                kd[i] = 65535u - (uint32_t)q;
+            }
+        }
+    }
+}
+
+__global__ void k_iota(uint32_t *__restrict__ x, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = (uint32_t)i;
+}
+
+__global__ void k_gather_items(const TileItem *__restrict__ in, const uint32_t *__restrict__ order,
+                               int64_t n, TileItem *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[order[i]];
+}
+
+// --------------------------------------------------------------------------- host helpers
+
+// Frees a list of pool allocations at scope exit.
+struct Scratch {
+    cudaStream_t st;
+    void *p[32];
+    int n = 0;
+    explicit Scratch(cudaStream_t s) : st(s) {}
+    template <class T>
+    bbc_status get(T **out, size_t count) {
+        bbc_status s = dev_alloc_n(out, count, st);
+        if (s == BBC_OK) p[n++] = *out;
+        return s;
+    }
+    ~Scratch() {
+        for (int i = 0; i < n; ++i) dev_free(p[i], st);
+    }
+};
+
+#define BBC_LAUNCH_CHECK(what)                                       \
+    do {                                                             \
+        cudaError_t _e = cudaGetLastError();                         \
+        if (_e != cudaSuccess) return ::bbc::cuda_fail(_e, what);    \
+    } while (0)
+
+// Ranks the vertices of one side by Def. 6; writes rank[id] and perm[rank] = id.
+bbc_status rank_side(const int32_t *deg, int64_t n, int32_t maxdeg, int32_t *rank, int32_t *perm,
+                     cudaStream_t st) {
+    if (n == 0) return BBC_OK;
+    Scratch sc(st);
+    uint32_t *k = nullptr, *vv = nullptr;
+    BBC_TRY(sc.get(&k, (size_t)n));
+    BBC_TRY(sc.get(&vv, (size_t)n));
+    k_rank_keys<<<grid_for(n), kThreads, 0, st>>>(deg, n, maxdeg, k, vv);
+    BBC_LAUNCH_CHECK("k_rank_keys");
+    BBC_TRY(radix_sort_pairs(k, vv, n, bit_length((uint64_t)maxdeg), st));
+    k_invert_perm<<<grid_for(n), kThreads, 0, st>>>(vv, n, rank, perm);
+    BBC_LAUNCH_CHECK("k_invert_perm");
+    return BBC_OK;
+}
+
+}  // namespace
+
+DevGraph host_descriptor(const bbc_graph *g, bool per_vertex) {
+    DevGraph d{};
+    d.rowS_off = g->rowS_off;
+    d.rowS = g->rowS;
+    d.rowC_off = g->rowC_off;
+    d.rowC = g->rowC;
+    d.nS = g->nS;
+    d.nC = g->nC;
+    d.orient_low = g->orient_low;
+    d.bS = per_vertex ? g->bS : nullptr;
+    d.bC = per_vertex ? g->bC : nullptr;
+    d.totals = g->totals;
+    d.wl = g->wl;
+    return d;
+}
+
+void release_graph(bbc_graph *g, cudaStream_t st) {
+    if (!g) return;
+    void *ptrs[] = {g->rowS_off, g->rowS, g->rowC_off, g->rowC, g->permS, g->permC, g->wl,
+                    g->tile_pack, g->tile_wide, g->warp_items, g->dgraph, g->bS, g->bC,
+                    g->totals, g->queue};
+    for (void *p : ptrs)
+        if (p) dev_free(p, st);
+    delete g;
+}
+
+bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
+    if (g->items_valid && g->items_tuning.tile_words == t.tile_words &&
+        g->items_tuning.warp_max_wedges == t.warp_max_wedges &&
+        g->items_tuning.split_wedges == t.split_wedges)
+        return BBC_OK;
+    if (g->tile_pack) dev_free(g->tile_pack, st);
+    if (g->tile_wide) dev_free(g->tile_wide, st);
+    if (g->warp_items) dev_free(g->warp_items, st);
+    g->tile_pack = g->tile_wide = nullptr;
+    g->warp_items = nullptr;
+    g->n_tile_pack = g->n_tile_wide = g->n_warp = 0;
+    g->items_valid = false;
+    const int64_t nS = g->nS;
+    if (nS == 0) {
+        g->items_tuning = t;
+        g->items_valid = true;
+        return BBC_OK;
+    }
+    Scratch sc(st);
+    int32_t *np = nullptr, *nw = nullptr, *nh = nullptr;
+    int64_t *pp = nullptr, *pw = nullptr, *ph = nullptr;
+    BBC_TRY(sc.get(&np, (size_t)nS));
+    BBC_TRY(sc.get(&nw, (size_t)nS));
+    BBC_TRY(sc.get(&nh, (size_t)nS));
+    BBC_TRY(sc.get(&pp, (size_t)nS + 1));
+    BBC_TRY(sc.get(&pw, (size_t)nS + 1));
+    BBC_TRY(sc.get(&ph, (size_t)nS + 1));
+    ClassifyParams P{g->nS, g->orient_low, t.tile_words, t.warp_max_wedges, t.split_wedges};
+    k_classify<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, np, nw, nh);
+    BBC_LAUNCH_CHECK("k_classify");
+    BBC_TRY(exclusive_scan_i32_to_i64(np, pp, nS, st));
+    BBC_TRY(exclusive_scan_i32_to_i64(nw, pw, nS, st));
+    BBC_TRY(exclusive_scan_i32_to_i64(nh, ph, nS, st));
+    int64_t counts[3];
+    BBC_CUDA_TRY(cudaMemcpyAsync(&counts[0], pp + nS, 8, cudaMemcpyDeviceToHost, st));
+    BBC_CUDA_TRY(cudaMemcpyAsync(&counts[1], pw + nS, 8, cudaMemcpyDeviceToHost, st));
+    BBC_CUDA_TRY(cudaMemcpyAsync(&counts[2], ph + nS, 8, cudaMemcpyDeviceToHost, st));
+    BBC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (counts[0] > INT32_MAX || counts[1] > INT32_MAX || counts[2] > INT32_MAX) {
+        set_error("work list longer than 2^31 items");
+        return BBC_E_INVALID_ARG;
+    }
+    TileItem *pack = nullptr, *wide = nullptr;
+    uint32_t *kp = nullptr, *kw = nullptr;
+    HashItem *warp = nullptr;
+    BBC_TRY(sc.get(&pack, (size_t)counts[0]));
+    BBC_TRY(sc.get(&kp, (size_t)counts[0]));
+    BBC_TRY(sc.get(&wide, (size_t)counts[1]));
+    BBC_TRY(sc.get(&kw, (size_t)counts[1]));
+    BBC_TRY(dev_alloc_n(&warp, (size_t)counts[2], st));
+    g->warp_items = warp;
+    g->n_warp = (int32_t)counts[2];
+    k_emit_items<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, pp, pw, ph, pack, kp,
+                                                     wide, kw, warp);
+    BBC_LAUNCH_CHECK("k_emit_items");
+    // Order the tile items by expected cost, largest first.
+    for (int which = 0; which < 2; ++which) {
+        const int64_t n = counts[which];
+        TileItem *src = which == 0 ? pack : wide;
+        uint32_t *keys = which == 0 ? kp : kw;
+        TileItem *dst = nullptr;
+        BBC_TRY(dev_alloc_n(&dst, (size_t)n, st));
+        if (which == 0) {
+            g->tile_pack = dst;
+            g->n_tile_pack = (int32_t)n;
+        } else {
+            g->tile_wide = dst;
+            g->n_tile_wide = (int32_t)n;
+        }
+        if (n == 0) continue;
+        uint32_t *order = nullptr;
+        BBC_TRY(sc.get(&order, (size_t)n));
+        k_iota<<<grid_for(n), kThreads, 0, st>>>(order, n);
+        BBC_LAUNCH_CHECK("k_iota");
+        BBC_TRY(radix_sort_pairs(keys, order, n, 16, st));
+        k_gather_items<<<grid_for(n), kThreads, 0, st>>>(src, order, n, dst);
+        BBC_LAUNCH_CHECK("k_gather_items");
+    }
+    g->items_tuning = t;
+    g->items_valid = true;
+    return BBC_OK;
+}
+
+bbc_status prepare_graph(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_t *u,
+                         const int32_t *v, const int8_t *sign, uint32_t flags, cudaStream_t st,
+                         bbc_graph **out) {
+    Scratch sc(st);
+    const int32_t *du = u, *dv = v;
+    const int8_t *ds = sign;
+    if (!(flags & BBC_INPUT_DEVICE) && n_edges > 0) {
+        int32_t *hu = nullptr, *hv = nullptr;
+        int8_t *hs = nullptr;
+        BBC_TRY(sc.get(&hu, (size_t)n_edges));
+        BBC_TRY(sc.get(&hv, (size_t)n_edges));
+        BBC_TRY(sc.get(&hs, (size_t)n_edges));
+        BBC_CUDA_TRY(cudaMemcpyAsync(hu, u, (size_t)n_edges * 4, cudaMemcpyHostToDevice, st));
+        BBC_CUDA_TRY(cudaMemcpyAsync(hv, v, (size_t)n_edges * 4, cudaMemcpyHostToDevice, st));
+        BBC_CUDA_TRY(cudaMemcpyAsync(hs, sign, (size_t)n_edges, cudaMemcpyHostToDevice, st));
+        du = hu;
+        dv = hv;
+        ds = hs;
+    }
+    // 1. validate + degrees
+    int32_t *deg_u = nullptr, *deg_v = nullptr;
+    unsigned long long *stats = nullptr;  // [0] err, [1..2] U stats, [3..4] V stats, [5] dups
+    BBC_TRY(sc.get(&deg_u, (size_t)n_u));
+    BBC_TRY(sc.get(&deg_v, (size_t)n_v));
+    BBC_TRY(sc.get(&stats, 8));
+    if (n_u > 0) BBC_CUDA_TRY(cudaMemsetAsync(deg_u, 0, (size_t)n_u * 4, st));
+    if (n_v > 0) BBC_CUDA_TRY(cudaMemsetAsync(deg_v, 0, (size_t)n_v * 4, st));
+    BBC_CUDA_TRY(cudaMemsetAsync(stats, 0, 64, st));
+    if (n_edges > 0) {
+        k_validate_degrees<<<grid_for(n_edges), kThreads, 0, st>>>(
+            du, dv, ds, n_edges, n_u, n_v, deg_u, deg_v, reinterpret_cast<unsigned *>(stats));
+        BBC_LAUNCH_CHECK("k_validate_degrees");
+    }
+    // 2. per-side sum of C(d,2) and max degree
+    if (n_u > 0) {
+        k_degree_stats<<<grid_for(n_u), kThreads, 0, st>>>(deg_u, n_u, stats + 1);
+        BBC_LAUNCH_CHECK("k_degree_stats");
+    }
+    if (n_v > 0) {
+        k_degree_stats<<<grid_for(n_v), kThreads, 0, st>>>(deg_v, n_v, stats + 3);
+        BBC_LAUNCH_CHECK("k_degree_stats");
+    }
+    unsigned long long hst[8];
+    BBC_CUDA_TRY(cudaMemcpyAsync(hst, stats, 64, cudaMemcpyDeviceToHost, st));
+    BBC_CUDA_TRY(cudaStreamSynchronize(st));
+    const unsigned err = (unsigned)(hst[0] & 0xffffffffu);
+    if (err & 1u) {
+        set_error("edge endpoint id out of range");
+        return BBC_E_OUT_OF_RANGE;
+    }
+    if (err & 2u) {
+        set_error("edge sign is not +1 or -1");
+        return BBC_E_BAD_SIGN;
+    }
+    const uint64_t c2_u = hst[1], c2_v = hst[3];
+    const int32_t max_u = (int32_t)hst[2], max_v = (int32_t)hst[4];
+    // Pair side S: pairs on U visit sum_{v in V} C(d_v, 2) wedges, pairs on V visit
+    // sum_{u in U} C(d_u, 2); the smaller wins (ties pick U).
+    int side = c2_v <= c2_u ? 0 : 1;
+    if (flags & BBC_SIDE_FORCE_U) side = 0;
+    if (flags & BBC_SIDE_FORCE_V) side = 1;
+    const int32_t nS = side == 0 ? n_u : n_v;
+    const int32_t nC = side == 0 ? n_v : n_u;
+    const int32_t *degS = side == 0 ? deg_u : deg_v;
+    const int32_t *degC = side == 0 ? deg_v : deg_u;
+    const int32_t maxS = side == 0 ? max_u : max_v;
+    const int32_t maxC = side == 0 ? max_v : max_u;
+    const uint64_t W = side == 0 ? c2_v : c2_u;
+    {
+        // balanced <= sum over pairs of C(c, 2) <= W * (max degree on S - 1) / 2
+        const unsigned __int128 bound = (unsigned __int128)W * (unsigned)(maxS > 0 ? maxS - 1 : 0) / 2;
+        if (bound > (unsigned __int128)UINT64_MAX) {
+            set_error("counts may exceed 2^64 - 1");
+            return BBC_E_OVERFLOW_RISK;
+        }
+    }
+
+    bbc_graph *g = new (std::nothrow) bbc_graph();
+    if (!g) {
+        set_error("host allocation failed");
+        return BBC_E_NO_MEMORY;
+    }
+    struct Guard {
+        bbc_graph *g;
+        cudaStream_t st;
+        ~Guard() {
+            if (g) release_graph(g, st);
+        }
+    } guard{g, st};
+    static std::atomic<uint64_t> next_uid{1};
+    g->uid = next_uid.fetch_add(1);
+    cudaGetDevice(&g->device);
+    g->n_u = n_u;
+    g->n_v = n_v;
+    g->side = side;
+    g->side_paper_rule = n_v < n_u ? 1 : 0;
+    g->orient_low = (flags & BBC_ORIENT_LOW_ANCHOR) ? 1 : 0;
+    g->nS = nS;
+    g->nC = nC;
+    g->wedges = W;
+    g->max_deg_S = maxS;
+    g->max_deg_C = maxC;
+
+    // 3. ranks
+    int32_t *rankS = nullptr, *rankC = nullptr;
+    BBC_TRY(sc.get(&rankS, (size_t)nS));
+    BBC_TRY(sc.get(&rankC, (size_t)nC));
+    BBC_TRY(dev_alloc_n(&g->permS, (size_t)nS, st));
+    BBC_TRY(dev_alloc_n(&g->permC, (size_t)nC, st));
+    BBC_TRY(rank_side(degS, nS, maxS, rankS, g->permS, st));
+    BBC_TRY(rank_side(degC, nC, maxC, rankC, g->permC, st));
+
+    // 4. the two CSR arrays
+    const int64_t E = n_edges;
+    uint32_t *kA = nullptr, *vA = nullptr, *kB = nullptr, *vB = nullptr;
+    BBC_TRY(sc.get(&kA, (size_t)E));
+    BBC_TRY(dev_alloc_n(&vA, (size_t)E, st));
+    g->rowS = vA;
+    BBC_TRY(sc.get(&kB, (size_t)E));
+    BBC_TRY(dev_alloc_n(&vB, (size_t)E, st));
+    g->rowC = vB;
+    if (E > 0) {
+        k_map_edges<<<grid_for(E), kThreads, 0, st>>>(du, dv, ds, E, side, rankS, rankC, kA, vA);
+        BBC_LAUNCH_CHECK("k_map_edges");
+        BBC_TRY(radix_sort_pairs(kA, vA, E, bit_length((uint64_t)(nS > 0 ? nS - 1 : 0)), st));
+        k_swap_sides<<<grid_for(E), kThreads, 0, st>>>(kA, vA, E, kB, vB);
+        BBC_LAUNCH_CHECK("k_swap_sides");
+        BBC_TRY(radix_sort_pairs(kB, vB, E, bit_length((uint64_t)(nC > 0 ? nC - 1 : 0)), st));
+        k_count_duplicates<<<grid_for(E), kThreads, 0, st>>>(kB, vB, E, stats + 5);
+        BBC_LAUNCH_CHECK("k_count_duplicates");
+        unsigned long long dups = 0;
+        BBC_CUDA_TRY(cudaMemcpyAsync(&dups, stats + 5, 8, cudaMemcpyDeviceToHost, st));
+        BBC_CUDA_TRY(cudaStreamSynchronize(st));
+        if (dups) {
+            if (!(flags & BBC_DEDUP_LAST)) {
+                set_error("duplicate (u, v) pair in the edge list");
+                return BBC_E_DUPLICATE_EDGE;
+            }
+            // Keep the last occurrence of each pair and prepare the de-duplicated list.
+            int32_t *flag = nullptr;
+            int64_t *pos = nullptr;
+            BBC_TRY(sc.get(&flag, (size_t)E));
+            BBC_TRY(sc.get(&pos, (size_t)E + 1));
+            k_last_flags<<<grid_for(E), kThreads, 0, st>>>(kB, vB, E, flag);
+            BBC_LAUNCH_CHECK("k_last_flags");
+            BBC_TRY(exclusive_scan_i32_to_i64(flag, pos, E, st));
+            const int64_t E2 = E - (int64_t)dups;
+            int32_t *u2 = nullptr, *v2 = nullptr;
+            int8_t *s2 = nullptr;
+            BBC_TRY(sc.get(&u2, (size_t)E2));
+            BBC_TRY(sc.get(&v2, (size_t)E2));
+            BBC_TRY(sc.get(&s2, (size_t)E2));
+            k_dedup_last<<<grid_for(E), kThreads, 0, st>>>(kB, vB, E, pos, side, g->permS, g->permC,
+                                                            u2, v2, s2);
+            BBC_LAUNCH_CHECK("k_dedup_last");
+            return prepare_graph(n_u, n_v, E2, u2, v2, s2,
+                                 (flags | BBC_INPUT_DEVICE) & ~(uint32_t)BBC_DEDUP_LAST, st, out);
+        }
+    }
+    g->n_edges = E;
+
+    // 5. row offsets from the ranked degrees
+    int32_t *dr = nullptr;
+    BBC_TRY(sc.get(&dr, (size_t)std::max(nS, nC)));
+    BBC_TRY(dev_alloc_n(&g->rowS_off, (size_t)nS + 1, st));
+    BBC_TRY(dev_alloc_n(&g->rowC_off, (size_t)nC + 1, st));
+    if (nS > 0) {
+        k_gather_deg<<<grid_for(nS), kThreads, 0, st>>>(degS, g->permS, nS, dr);
+        BBC_LAUNCH_CHECK("k_gather_deg");
+    }
+    BBC_TRY(exclusive_scan_i32_to_i64(dr, g->rowS_off, nS, st));
+    if (nC > 0) {
+        k_gather_deg<<<grid_for(nC), kThreads, 0, st>>>(degC, g->permC, nC, dr);
+        BBC_LAUNCH_CHECK("k_gather_deg");
+    }
+    BBC_TRY(exclusive_scan_i32_to_i64(dr, g->rowC_off, nC, st));
+
+    // 6. oriented wedges per anchor
+    BBC_TRY(dev_alloc_n(&g->wl, (size_t)nS, st));
+    if (nS > 0) BBC_CUDA_TRY(cudaMemsetAsync(g->wl, 0, (size_t)nS * 8, st));
+    if (E > 0) {
+        k_wedge_estimate<<<grid_for(E), kThreads, 0, st>>>(kA, g->rowS, E, g->rowC_off, g->rowC,
+                                                             g->orient_low, g->wl);
+        BBC_LAUNCH_CHECK("k_wedge_estimate");
+    }
+    BBC_TRY(dev_alloc_n(&g->totals, 2, st));
+    BBC_TRY(dev_alloc_n(&g->queue, 1, st));
+    BBC_TRY(dev_alloc_n(&g->dgraph, 1, st));
+    g->device_bytes = (size_t)(nS + 1 + nC + 1) * 8 + (size_t)E * 8 + (size_t)(nS + nC) * 4 +
+                      (size_t)nS * 8;
+    *out = g;
+    guard.g = nullptr;
+    return BBC_OK;
+}
+
+}  // namespace bbc
