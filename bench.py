@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Throughput of exact balanced-butterfly counting on one GB300 (or N replicas).
+
+One step is the whole hot path over one synthetic graph: bbc_prepare (validation,
+degrees, pair-side choice, rank relabelling, the two signed CSR arrays, per-anchor wedge
+estimate, work lists) followed by bbc_count with global and per-vertex counts. The
+workload is the Chung-Lu power-law graph |U| = 1,000,000, |V| = 200,000, 20,000,000
+distinct edges, expected-degree exponent 2.2 on both sides (max 50,000), P(+) = 0.8,
+seed 0. The metric is W / step time in wedges per second, where W is the number of
+oriented wedges of the graph (the sum over the centre side of C(d, 2)).
+
+  value  device-resident input (edge list already in HBM), as the library sees it
+  e2e    the same through host buffers: pinned host edge list copied in, per-vertex
+         counts and totals copied out, every step inside the timed region
+  roofline  the tile kernel's algorithmic bytes per launch (4 B per wedge visit, two
+         visits per wedge with per-vertex counts, plus 20 B per edge) over its average
+         launch time, from CUDA events recorded around each launch on its own stream
+  cpu_baseline  the CPU oracle on a strided anchor sample of the same graph
+
+--impl reference times the CPU oracle (the only reference implementation of this
+method) on the host cores instead. Multi-GPU runs (torchrun) count one replica of the
+workload per GPU, with no data-path collective (weak scaling).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "wedges/sec & % HBM roofline; batched graphs/sec vs per-graph launches"
+UNIT = "wedges/s"
+WORKLOAD = "powerlaw_1m_200k_20m"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_tile_powerlaw_1m_200k_20m.traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_digest() -> str:
+    h = hashlib.sha256()
+    for name in ("count.cu", "bbc_internal.cuh", "graph.cuh"):
+        with open(os.path.join(ROOT, "paper_2601_17707_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes of the tile kernel from the committed ncu summary, or None
+    when the kernel source changed since that capture."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    if rec.get("source_sha256") != kernel_source_digest():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in (self.out or "").splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, p[5:9]):
+                if val.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload():
+    from paper_2601_17707_gb300 import synth
+
+    return synth.powerlaw_1m_200k(seed=0)
+
+
+def oracle_sample(g, target_s: float):
+    """Times the oracle on a strided anchor sample sized for about target_s seconds.
+    Returns (wedges per second, wedges visited, seconds, threads, stride)."""
+    import oracle
+
+    threads = os.cpu_count() or 1
+
+    def run(stride):
+        t0 = time.perf_counter()
+        _, w = oracle.count_sample(g, stride=stride, threads=threads, per_vertex=True)
+        return w, time.perf_counter() - t0
+
+    stride = 8192
+    w, dt = run(stride)
+    while dt < 0.5 and stride > 1:
+        stride = max(1, stride // 8)
+        w, dt = run(stride)
+    stride = max(1, int(stride * dt / target_s))
+    w, dt = run(stride)
+    return w / dt, w, dt, threads, stride
+
+
+def bench_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    g = make_workload()
+    threads = os.cpu_count() or 1
+    # size the per-step sample so that warmup + steps stay within a few minutes
+    per_step = max(2.0, min(15.0, 150.0 / max(1, args.steps + args.warmup)))
+    rate, w, dt, threads, stride = oracle_sample(g, per_step)
+    for _ in range(args.warmup):
+        oracle.count_sample(g, stride=stride, threads=threads, per_vertex=True)
+    times, visited = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _, w = oracle.count_sample(g, stride=stride, threads=threads, per_vertex=True)
+        times.append(time.perf_counter() - t0)
+        visited += w
+    total = sum(times)
+    value = visited / total
+    sample = (f"CPU oracle (bbc_oracle.c, {threads} threads) over every {stride}-th anchor of U "
+              f"with per-vertex counts; {visited // max(1, args.steps)} oriented wedges per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n_u": g.n_u, "n_v": g.n_v,
+                                        "n_edges": g.n_edges, "seed": 0, "sample_stride": stride},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def bench_gpu(args):
+    import torch
+
+    from paper_2601_17707_gb300 import _build, bbc
+
+    world, rank, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    _build.build()
+    bbc.load()
+    g = make_workload()
+    dev = torch.device("cuda", local)
+    u_h = torch.from_numpy(g.u).pin_memory()
+    v_h = torch.from_numpy(g.v).pin_memory()
+    s_h = torch.from_numpy(g.sign).pin_memory()
+    u_d, v_d, s_d = u_h.to(dev), v_h.to(dev), s_h.to(dev)
+    per_u = torch.empty(g.n_u, dtype=torch.int64, device=dev)
+    per_v = torch.empty(g.n_v, dtype=torch.int64, device=dev)
+    per_u_h = torch.empty(g.n_u, dtype=torch.int64).pin_memory()
+    per_v_h = torch.empty(g.n_v, dtype=torch.int64).pin_memory()
+    totals = torch.empty(2, dtype=torch.int64, device=dev)
+    totals_h = torch.empty(2, dtype=torch.int64).pin_memory()
+    stream = torch.cuda.current_stream(dev)
+
+    G0 = bbc.Graph.prepare(g.n_u, g.n_v, u_d, v_d, s_d)
+    info = G0.info()
+    G0.free()
+    W = info.wedges
+
+    def step_device():
+        G = bbc.Graph.prepare(g.n_u, g.n_v, u_d, v_d, s_d)
+        G.count_async(totals, per_u, per_v)
+        G.free()
+
+    def step_host():
+        # the public call with host buffers: H2D of the edge list inside bbc_prepare
+        G = bbc.Graph.prepare(g.n_u, g.n_v, u_h.numpy(), v_h.numpy(), s_h.numpy())
+        G.count_async(totals, per_u, per_v)
+        per_u_h.copy_(per_u, non_blocking=True)
+        per_v_h.copy_(per_v, non_blocking=True)
+        totals_h.copy_(totals, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        G.free()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed(fn, steps):
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize(dev)
+    launches0 = bbc.launch_count()
+    bbc.profile_start()
+    with ClockSampler(local) as clk:
+        ms = timed(step_device, args.steps)
+    prof = bbc.profile_stop()
+    launches = bbc.launch_count() - launches0
+    # correctness of what was timed: the last step's totals against a fresh count
+    b_last = int(totals[0].item())
+
+    e2e = None
+    if not args.no_e2e:
+        for _ in range(max(1, args.warmup // 2)):
+            step_host()
+        ms_e2e = timed(step_host, args.steps)
+        e2e = {"value": world * W * args.steps / (ms_e2e / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": g.n_edges * (4 + 4 + 1),
+               "d2h_bytes_per_step": (g.n_u + g.n_v) * 8 + 16, "ms_per_step": ms_e2e / args.steps}
+
+    tile_launches, tile_ms = prof.get("k_tile", (0, 0.0))
+    peak, peak_kind = hbm_peak()
+    roof = None
+    if tile_launches:
+        alg_bytes = 4 * 2 * W + 20 * g.n_edges   # per launch (one launch per step)
+        per_launch_s = tile_ms / tile_launches / 1e3
+        achieved = alg_bytes / per_launch_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": recorded_traffic(),
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s", "kernel": "k_tile",
+                "kernel_ms_per_launch": tile_ms / tile_launches,
+                "algorithmic_bytes_per_launch": alg_bytes}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, w, dt, threads, stride = oracle_sample(g, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"every {stride}-th anchor of U with per-vertex counts: {w} oriented "
+                         f"wedges in {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * W * args.steps / (ms / 1e3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_u": g.n_u, "n_v": g.n_v, "n_edges": g.n_edges,
+                       "wedges": W, "pair_side": "V" if info.side == 1 else "U", "seed": 0,
+                       "per_vertex": True, "step": "bbc_prepare + bbc_count (global + per-vertex)",
+                       "l2": "inputs larger than L2: 180 MB edge list, 170 MB CSR per step",
+                       "parallelism": f"replicas x{world}", "balanced": b_last},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+            "gpu_launches": launches, "kernel_profile": prof,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

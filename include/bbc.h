@@ -195,6 +195,24 @@ bbc_status bbc_server_stats(bbc_server *s, uint64_t *completed, double *p50_us,
 /* Stops the loop; requests still queued finish with BBC_E_CANCELLED. */
 void bbc_server_destroy(bbc_server *s);
 
+/*
+ * Accounting for reports (not part of the counting): bbc_launch_count is the number of
+ * CUDA kernels this library has launched in this process. Between bbc_profile_start and
+ * bbc_profile_stop every launch of a counting kernel (outside stream capture) is
+ * bracketed by CUDA events on its own stream; bbc_profile_stop waits for them and fills
+ * up to `capacity` entries, one per kernel, with its launches and summed device time
+ * (*count receives the number of kernels seen).
+ */
+typedef struct bbc_kernel_time {
+    const char *name;    /* static string */
+    int64_t launches;
+    double total_ms;
+} bbc_kernel_time;
+
+unsigned long long bbc_launch_count(void);
+bbc_status bbc_profile_start(void);
+bbc_status bbc_profile_stop(bbc_kernel_time *out, int32_t capacity, int32_t *count);
+
 /* Static strings; never NULL. */
 const char *bbc_status_string(bbc_status st);
 const char *bbc_last_error(void);

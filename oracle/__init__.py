@@ -69,6 +69,9 @@ def _lib(mutant: int = 0) -> ctypes.CDLL:
             lib.bbco_count.argtypes = [i32, i32, i64, p, p, p, ctypes.c_int, ctypes.c_int,
                                        p, p, p, p]
             lib.bbco_count.restype = ctypes.c_int
+            lib.bbco_count_sample.argtypes = [i32, i32, i64, p, p, p, ctypes.c_int, ctypes.c_int,
+                                              i64, i64, p, p, p, p, p]
+            lib.bbco_count_sample.restype = ctypes.c_int
             lib.bbco_vertex.argtypes = [i32, i32, i64, p, p, p, ctypes.c_int, i32, p]
             lib.bbco_vertex.restype = ctypes.c_int
             lib.bbco_mutant.restype = ctypes.c_int
@@ -110,6 +113,26 @@ def count(g, orient_low: bool = False, threads: int = 1, per_vertex: bool = True
     if st != 0:
         raise ValueError(f"oracle: {STATUS.get(st, st)}")
     return Counts(int(b.value), int(ub.value), pu, pv)
+
+
+def count_sample(g, stride: int, offset: int = 0, threads: int = 1, per_vertex: bool = True):
+    """The oracle over the anchors offset, offset + stride, ... of U only (a bounded
+    sample of the full count, for timing). Returns (Counts, oriented wedges visited)."""
+    lib = _lib(0)
+    u, v, s = _arrays(g)
+    b = ctypes.c_uint64(0)
+    ub = ctypes.c_uint64(0)
+    w = ctypes.c_uint64(0)
+    pu = np.zeros(g.n_u, dtype=np.uint64) if per_vertex else None
+    pv = np.zeros(g.n_v, dtype=np.uint64) if per_vertex else None
+    st = lib.bbco_count_sample(g.n_u, g.n_v, u.shape[0], u.ctypes.data, v.ctypes.data,
+                               s.ctypes.data, 0, int(threads), int(offset), int(stride),
+                               ctypes.addressof(b), ctypes.addressof(ub),
+                               pu.ctypes.data if pu is not None else None,
+                               pv.ctypes.data if pv is not None else None, ctypes.addressof(w))
+    if st != 0:
+        raise ValueError(f"oracle: {STATUS.get(st, st)}")
+    return Counts(int(b.value), int(ub.value), pu, pv), int(w.value)
 
 
 def vertex(g, side: int, x: int, mutant: int = 0) -> int:

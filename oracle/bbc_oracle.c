@@ -122,7 +122,8 @@ typedef struct {
     int orient_low;
     /* shared, written with atomics */
     uint64_t *per_u, *per_v;
-    int64_t next_anchor;
+    int64_t next_anchor;       /* index into the sampled anchors */
+    int64_t anchor_offset, anchor_stride, n_anchors;
     /* per-thread results */
     u128 balanced, unbalanced;
     int status;
@@ -131,6 +132,7 @@ typedef struct {
 typedef struct {
     job_t *job;
     u128 balanced, unbalanced;
+    uint64_t wedges;           /* oriented wedges visited in the wedge pass */
     int status;
 } worker_t;
 
@@ -153,8 +155,9 @@ static void *worker(void *arg) {
         return NULL;
     }
     for (;;) {
-        int64_t u = __atomic_fetch_add(&jb->next_anchor, 1, __ATOMIC_RELAXED);
-        if (u >= jb->n_u) break;
+        int64_t i_anchor = __atomic_fetch_add(&jb->next_anchor, 1, __ATOMIC_RELAXED);
+        if (i_anchor >= jb->n_anchors) break;
+        int64_t u = jb->anchor_offset + i_anchor * jb->anchor_stride;
         int64_t n_touched = 0;
         /* Wedge pass: bucket every oriented wedge u-v-w by its endpoint and type. */
         for (int64_t i = au->off[u]; i < au->off[u + 1]; ++i) {
@@ -163,6 +166,7 @@ static void *worker(void *arg) {
             for (int64_t j = av->off[v]; j < av->off[v + 1]; ++j) {
                 int32_t w = av->nbr[j];
                 if (!oriented((int32_t)u, w, jb->orient_low)) continue;
+                wk->wedges++;
                 if (sym[w] == 0 && asym[w] == 0) touched[n_touched++] = w;
                 if (wedge_symmetric(s1, av->sgn[j]))
                     sym[w]++;
@@ -220,16 +224,21 @@ static void *worker(void *arg) {
 }
 
 /*
- * Counts balanced and unbalanced butterflies of the signed bipartite graph given by
- * its edge list (ids 0-based per side, signs +1 / -1, no duplicate pairs).
+ * Counts, over the anchors u = offset, offset + stride, ... of side U, the balanced and
+ * unbalanced butterflies closed at those anchors (with stride 1 and offset 0: all
+ * butterflies of the graph). The graph is given by its edge list (ids 0-based per side,
+ * signs +1 / -1, no duplicate pairs).
  *   per_u (n_u entries) and per_v (n_v entries) may be NULL; when given they are
- *   overwritten with the per-vertex balanced counts.
+ *   overwritten with the per-vertex balanced counts (complete only for stride 1).
  *   n_threads <= 1 runs on the calling thread only.
+ *   wedges (may be NULL) receives the number of oriented wedges visited.
  * Returns BBCO_OK, BBCO_BAD_INPUT, BBCO_NO_MEMORY or BBCO_OVERFLOW.
  */
-int bbco_count(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_t *eu, const int32_t *ev,
-               const int8_t *es, int orient_low, int n_threads, uint64_t *balanced,
-               uint64_t *unbalanced, uint64_t *per_u, uint64_t *per_v) {
+int bbco_count_sample(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_t *eu,
+                      const int32_t *ev, const int8_t *es, int orient_low, int n_threads,
+                      int64_t anchor_offset, int64_t anchor_stride, uint64_t *balanced,
+                      uint64_t *unbalanced, uint64_t *per_u, uint64_t *per_v, uint64_t *wedges) {
+    if (anchor_stride < 1 || anchor_offset < 0) return BBCO_BAD_INPUT;
     int st = check_input(n_u, n_v, n_edges, eu, ev, es);
     if (st) return st;
     adj_t au, av;
@@ -249,6 +258,9 @@ int bbco_count(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_t *eu, con
     jb.orient_low = orient_low;
     jb.per_u = per_u;
     jb.per_v = per_v;
+    jb.anchor_offset = anchor_offset;
+    jb.anchor_stride = anchor_stride;
+    jb.n_anchors = anchor_offset < n_u ? (n_u - 1 - anchor_offset) / anchor_stride + 1 : 0;
     if (n_threads < 1) n_threads = 1;
     worker_t *wk = (worker_t *)calloc((size_t)n_threads, sizeof(worker_t));
     pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
@@ -274,10 +286,12 @@ int bbco_count(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_t *eu, con
         for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
     }
     u128 b = 0, ub = 0;
+    uint64_t visited = 0;
     st = BBCO_OK;
     for (int t = 0; t < n_threads; ++t) {
         b += wk[t].balanced;
         ub += wk[t].unbalanced;
+        visited += wk[t].wedges;
         if (wk[t].status) st = wk[t].status;
     }
     free(wk);
@@ -288,7 +302,16 @@ int bbco_count(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_t *eu, con
     if (b > (u128)UINT64_MAX || ub > (u128)UINT64_MAX) return BBCO_OVERFLOW;
     *balanced = (uint64_t)b;
     *unbalanced = (uint64_t)ub;
+    if (wedges) *wedges = visited;
     return BBCO_OK;
+}
+
+/* The whole graph: every anchor of U. */
+int bbco_count(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_t *eu, const int32_t *ev,
+               const int8_t *es, int orient_low, int n_threads, uint64_t *balanced,
+               uint64_t *unbalanced, uint64_t *per_u, uint64_t *per_v) {
+    return bbco_count_sample(n_u, n_v, n_edges, eu, ev, es, orient_low, n_threads, 0, 1,
+                             balanced, unbalanced, per_u, per_v, NULL);
 }
 
 /*

@@ -36,7 +36,7 @@ EXPORTS = (
     "bbc_tuning_default", "bbc_prepare", "bbc_count", "bbc_count_async", "bbc_graph_info",
     "bbc_graph_free", "bbc_count_batch", "bbc_autotune_batch", "bbc_server_create", "bbc_submit",
     "bbc_poll", "bbc_wait", "bbc_server_stats", "bbc_server_destroy", "bbc_status_string",
-    "bbc_last_error",
+    "bbc_last_error", "bbc_launch_count", "bbc_profile_start", "bbc_profile_stop",
 )
 
 
@@ -44,6 +44,10 @@ class BBCError(RuntimeError):
     def __init__(self, status: int, where: str, detail: str = ""):
         self.status = status
         super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} ({detail})")
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
 class Tuning(ctypes.Structure):
@@ -96,6 +100,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                  ctypes.c_int),
             "bbc_server_destroy": ([vp], None),
             "bbc_status_string": ([ctypes.c_int], ctypes.c_char_p),
+            "bbc_launch_count": ([], ctypes.c_ulonglong),
+            "bbc_profile_start": ([], ctypes.c_int),
+            "bbc_profile_stop": ([ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)], ctypes.c_int),
             "bbc_last_error": ([], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
@@ -104,6 +111,24 @@ def load(path: str | None = None) -> ctypes.CDLL:
             fn.restype = res
         _LIB = lib
         return lib
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().bbc_launch_count())
+
+
+def profile_start() -> None:
+    check(load().bbc_profile_start(), "bbc_profile_start")
+
+
+def profile_stop() -> dict:
+    """{kernel name: (launches, total device ms)} since profile_start."""
+    arr = (KernelTime * 8)()
+    n = ctypes.c_int32()
+    check(load().bbc_profile_stop(arr, 8, ctypes.byref(n)), "bbc_profile_stop")
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
+            for i in range(min(n.value, 8))}
 
 
 def last_error() -> str:

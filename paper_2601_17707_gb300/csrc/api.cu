@@ -1,6 +1,8 @@
 // api.cu -- the extern "C" entry points of include/bbc.h for single graphs, plus the
 // library's error state, memory pool and tuning defaults.
 #include <algorithm>
+#include <atomic>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -77,6 +79,42 @@ bbc_status check_device() {
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+std::atomic<bool> g_prof_on{false};
+std::mutex g_prof_mu;
+struct ProfSlot {
+    cudaEvent_t a = nullptr, b = nullptr;
+    int kind = 0;
+    bool used = false;
+};
+std::vector<ProfSlot> g_prof;
+const char *const kProfNames[kProfKinds] = {"k_tile", "k_warp_hash"};
+}  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int profile_begin(int kind, cudaStream_t st) {
+    if (!g_prof_on.load(std::memory_order_relaxed)) return -1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return -1;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfSlot sl;
+    if (cudaEventCreate(&sl.a) != cudaSuccess || cudaEventCreate(&sl.b) != cudaSuccess) return -1;
+    sl.kind = kind;
+    cudaEventRecord(sl.a, st);
+    g_prof.push_back(sl);
+    return (int)g_prof.size() - 1;
+}
+
+void profile_end(int token, cudaStream_t st) {
+    if (token < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (token >= (int)g_prof.size()) return;
+    cudaEventRecord(g_prof[token].b, st);
+    g_prof[token].used = true;
+}
+
 bbc_status cuda_fail(cudaError_t e, const char *what) {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
     if (e == cudaErrorMemoryAllocation) return BBC_E_NO_MEMORY;
@@ -110,7 +148,7 @@ int device_sm_count() {
 Tuning resolve_tuning(const bbc_tuning *t, int sm_count) {
     (void)sm_count;
     Tuning r;
-    r.tile_words = 26624;
+    r.tile_words = 0;  // 0: the largest tile that keeps blocks_per_sm blocks resident
     r.warp_max_wedges = 256;
     r.dense_min_permille = 0;
     r.split_wedges = 0;  // 0: chosen per launch from the total work
@@ -122,10 +160,12 @@ Tuning resolve_tuning(const bbc_tuning *t, int sm_count) {
         if (t->dense_min_permille > 0) r.dense_min_permille = t->dense_min_permille;
         if (t->split_wedges > 0) r.split_wedges = t->split_wedges;
     }
-    // limits: tiles are whole 16-byte groups and fit the per-block shared memory of the
-    // chosen residency; hash tables hold at most 512 wedges
-    const int cap = r.blocks_per_sm == 1 ? 53248 : 26624;
-    if (r.tile_words > cap) r.tile_words = cap;
+    // limits: tiles are whole 32-byte groups and fit the shared memory an SM gives each
+    // of blocks_per_sm resident blocks (228 KB per SM, 1 KB reserved per block, minus
+    // the kernel's static shared memory); hash tables hold at most 512 wedges
+    const int per_block = (228 * 1024) / r.blocks_per_sm - 1024 - tile_static_smem_bytes();
+    const int cap = std::min(per_block, 227 * 1024 - tile_static_smem_bytes()) / 4;
+    if (r.tile_words == 0 || r.tile_words > cap) r.tile_words = cap;
     if (r.tile_words < 1024) r.tile_words = 1024;
     r.tile_words &= ~7;
     if (r.warp_max_wedges > 512) r.warp_max_wedges = 512;
@@ -159,14 +199,13 @@ bbc_status count_graph(bbc_graph *g, uint64_t *totals_dev, uint64_t *per_u, uint
     BBC_CUDA_TRY(cudaMemsetAsync(g->queue, 0, sizeof(QueueState), st));
     static_assert(sizeof(DevGraph) % 8 == 0, "descriptor layout");
     DevGraph d = host_descriptor(g, pv);
+    note_launch();
     k_store_descriptor<<<1, 1, 0, st>>>(d, g->dgraph);
     BBC_CUDA_TRY(cudaGetLastError());
     CountLaunch L{};
     L.graphs = g->dgraph;
-    L.tile_items = g->tile_pack;
-    L.n_tile_items = g->n_tile_pack;
-    L.wide_items = g->tile_wide;
-    L.n_wide_items = g->n_tile_wide;
+    L.tile_items = g->tile_items;
+    L.n_tile_items = g->n_tile;
     L.warp_items = g->warp_items;
     L.n_warp_items = g->n_warp;
     L.queue = g->queue;
@@ -176,11 +215,13 @@ bbc_status count_graph(bbc_graph *g, uint64_t *totals_dev, uint64_t *per_u, uint
         uint64_t *outS = g->side == 0 ? per_u : per_v;
         uint64_t *outC = g->side == 0 ? per_v : per_u;
         if (outS && g->nS) {
+            note_launch();
             k_scatter_per_vertex<<<(unsigned)std::min<int64_t>((g->nS + 255) / 256, 4096), 256, 0, st>>>(
                 g->bS, g->permS, g->nS, reinterpret_cast<unsigned long long *>(outS));
             BBC_CUDA_TRY(cudaGetLastError());
         }
         if (outC && g->nC) {
+            note_launch();
             k_scatter_per_vertex<<<(unsigned)std::min<int64_t>((g->nC + 255) / 256, 4096), 256, 0, st>>>(
                 g->bC, g->permC, g->nC, reinterpret_cast<unsigned long long *>(outC));
             BBC_CUDA_TRY(cudaGetLastError());
@@ -303,6 +344,52 @@ bbc_status bbc_count(bbc_graph *g, uint64_t *balanced, uint64_t *unbalanced, uin
         set_error("unexpected exception in bbc_count");
         return BBC_E_CUDA;
     }
+}
+
+unsigned long long bbc_launch_count(void) { return g_launches.load(); }
+
+bbc_status bbc_profile_start(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (ProfSlot &sl : g_prof) {
+        cudaEventDestroy(sl.a);
+        cudaEventDestroy(sl.b);
+    }
+    g_prof.clear();
+    g_prof_on.store(true);
+    return BBC_OK;
+}
+
+bbc_status bbc_profile_stop(bbc_kernel_time *out, int32_t capacity, int32_t *count) {
+    g_prof_on.store(false);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    long long launches[kProfKinds] = {0};
+    double ms[kProfKinds] = {0};
+    bbc_status st = BBC_OK;
+    for (ProfSlot &sl : g_prof) {
+        if (sl.used) {
+            cudaError_t e = cudaEventSynchronize(sl.b);
+            float t = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, sl.a, sl.b);
+            if (e != cudaSuccess) st = cuda_fail(e, "bbc_profile_stop");
+            launches[sl.kind] += 1;
+            ms[sl.kind] += t;
+        }
+        cudaEventDestroy(sl.a);
+        cudaEventDestroy(sl.b);
+    }
+    g_prof.clear();
+    int n = 0;
+    for (int k = 0; k < kProfKinds; ++k) {
+        if (!launches[k]) continue;
+        if (out && n < capacity) {
+            out[n].name = kProfNames[k];
+            out[n].launches = launches[k];
+            out[n].total_ms = ms[k];
+        }
+        ++n;
+    }
+    if (count) *count = n;
+    return st;
 }
 
 bbc_status bbc_graph_info(const bbc_graph *g, int32_t *side, uint64_t *wedges,

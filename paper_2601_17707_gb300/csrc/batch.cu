@@ -42,15 +42,17 @@ __global__ void k_concat_items(const CopyJob *__restrict__ jobs, Item *__restric
 
 // 16-bit key ordering tile items by expected wedges, largest first, across graphs.
 __global__ void k_tile_item_keys(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items,
-                                 int64_t n, int ept, uint32_t *__restrict__ keys,
+                                 int64_t n, int tile_words, uint32_t *__restrict__ keys,
                                  uint32_t *__restrict__ order) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const TileItem it = items[i];
         const DevGraph &G = graphs[it.graph];
+        const int cw = tile_width_of(it);
+        const long long ept = cw == 0 ? 2ll * tile_words : (cw == 1 ? tile_words : tile_words / 2);
         const long long span = G.orient_low ? it.anchor : (long long)G.nS - 1 - it.anchor;
         const long long nt = (span + ept - 1) / ept;
-        const double cost = (double)G.wl[it.anchor] * (double)(it.tile_end - it.tile_begin) /
+        const double cost = (double)G.wl[it.anchor] * (double)(tile_end_of(it) - it.tile_begin) /
                                 (double)(nt > 0 ? nt : 1) + 1.0;
         int q = (int)(log2(cost) * 1024.0);
         q = q < 0 ? 0 : (q > 65535 ? 65535 : q);
@@ -75,16 +77,16 @@ struct Plan {
     unsigned long long *totals = nullptr;     // 2 per graph
     unsigned long long *host_totals = nullptr;  // pinned
     QueueState *queue = nullptr;
-    TileItem *pack = nullptr, *wide = nullptr;
+    TileItem *tiles = nullptr;
     HashItem *warp = nullptr;
-    int32_t n_pack = 0, n_wide = 0, n_warp = 0;
+    int32_t n_tile = 0, n_warp = 0;
     cudaStream_t stream = nullptr;            // capture / replay stream
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t exec = nullptr;
 
     ~Plan() {
         if (exec) cudaGraphExecDestroy(exec);
-        void *ps[] = {dgraphs, totals, queue, pack, wide, warp};
+        void *ps[] = {dgraphs, totals, queue, tiles, warp};
         for (void *p : ps)
             if (p) dev_free(p, stream);
         if (stream) cudaStreamSynchronize(stream);
@@ -150,43 +152,39 @@ bbc_status build_plan(int32_t n, bbc_graph *const *gs, const Tuning &T, std::uni
         BBC_TRY(build_work_lists(gs[i], T, st));
     }
     std::vector<DevGraph> hd(n);
-    std::vector<CopyJob> jp, jw, jh;
-    int64_t np = 0, nw = 0, nh = 0;
+    std::vector<CopyJob> jt, jh;
+    int64_t nt = 0, nh = 0;
     BBC_TRY(dev_alloc_n(&P->totals, (size_t)2 * n, st));
     for (int i = 0; i < n; ++i) {
         bbc_graph *g = gs[i];
         hd[i] = host_descriptor(g, false);
         hd[i].totals = P->totals + 2 * i;
-        if (g->n_tile_pack) jp.push_back(CopyJob{g->tile_pack, np, g->n_tile_pack, i});
-        if (g->n_tile_wide) jw.push_back(CopyJob{g->tile_wide, nw, g->n_tile_wide, i});
+        if (g->n_tile) jt.push_back(CopyJob{g->tile_items, nt, g->n_tile, i});
         if (g->n_warp) jh.push_back(CopyJob{g->warp_items, nh, g->n_warp, i});
-        np += g->n_tile_pack;
-        nw += g->n_tile_wide;
+        nt += g->n_tile;
         nh += g->n_warp;
     }
-    if (np > INT32_MAX || nw > INT32_MAX || nh > INT32_MAX) {
+    if (nt > INT32_MAX || nh > INT32_MAX) {
         set_error("bbc_count_batch: too many work items");
         return BBC_E_INVALID_ARG;
     }
-    P->n_pack = (int32_t)np;
-    P->n_wide = (int32_t)nw;
+    P->n_tile = (int32_t)nt;
     P->n_warp = (int32_t)nh;
     BBC_TRY(dev_alloc_n(&P->dgraphs, (size_t)n, st));
     BBC_TRY(dev_alloc_n(&P->queue, 1, st));
-    BBC_TRY(dev_alloc_n(&P->pack, (size_t)np, st));
-    BBC_TRY(dev_alloc_n(&P->wide, (size_t)nw, st));
+    BBC_TRY(dev_alloc_n(&P->tiles, (size_t)nt, st));
     BBC_TRY(dev_alloc_n(&P->warp, (size_t)nh, st));
     BBC_CUDA_TRY(cudaMallocHost(&P->host_totals, sizeof(unsigned long long) * 2 * (size_t)std::max(n, 1)));
     BBC_CUDA_TRY(cudaMemcpyAsync(P->dgraphs, hd.data(), sizeof(DevGraph) * (size_t)n,
                                  cudaMemcpyHostToDevice, st));
     // concatenate, tagging each item with its graph index
     CopyJob *djobs = nullptr;
-    const size_t maxj = std::max(jp.size(), std::max(jw.size(), jh.size()));
+    const size_t maxj = std::max(jt.size(), jh.size());
     BBC_TRY(dev_alloc_n(&djobs, maxj, st));
     struct Part {
         std::vector<CopyJob> *jobs;
         int which;
-    } parts[3] = {{&jp, 0}, {&jw, 1}, {&jh, 2}};
+    } parts[2] = {{&jt, 0}, {&jh, 2}};
     bbc_status s = BBC_OK;
     for (auto &pt : parts) {
         if (pt.jobs->empty()) continue;
@@ -197,8 +195,8 @@ bbc_status build_plan(int32_t n, bbc_graph *const *gs, const Tuning &T, std::uni
             break;
         }
         const unsigned nb = (unsigned)pt.jobs->size();
-        if (pt.which == 0) k_concat_items<TileItem><<<nb, kThreads, 0, st>>>(djobs, P->pack);
-        if (pt.which == 1) k_concat_items<TileItem><<<nb, kThreads, 0, st>>>(djobs, P->wide);
+        note_launch();
+        if (pt.which == 0) k_concat_items<TileItem><<<nb, kThreads, 0, st>>>(djobs, P->tiles);
         if (pt.which == 2) k_concat_items<HashItem><<<nb, kThreads, 0, st>>>(djobs, P->warp);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // djobs is reused
@@ -210,39 +208,34 @@ bbc_status build_plan(int32_t n, bbc_graph *const *gs, const Tuning &T, std::uni
     dev_free(djobs, st);
     BBC_TRY(s);
     // order tile items across graphs, heaviest first
-    for (int which = 0; which < 2; ++which) {
-        const int64_t cnt = which == 0 ? np : nw;
-        if (cnt <= 1) continue;
-        TileItem *items = which == 0 ? P->pack : P->wide;
-        const int ept = which == 0 ? T.tile_words : T.tile_words / 2;
+    if (nt > 1) {
+        const int64_t cnt = nt;
+        TileItem *items = P->tiles;
         uint32_t *keys = nullptr, *order = nullptr;
         TileItem *sorted = nullptr;
         BBC_TRY(dev_alloc_n(&keys, (size_t)cnt, st));
         BBC_TRY(dev_alloc_n(&order, (size_t)cnt, st));
         BBC_TRY(dev_alloc_n(&sorted, (size_t)cnt, st));
         const unsigned grid = (unsigned)std::min<int64_t>((cnt + kThreads - 1) / kThreads, 4096);
-        k_tile_item_keys<<<grid, kThreads, 0, st>>>(P->dgraphs, items, cnt, ept, keys, order);
+        note_launch();
+        k_tile_item_keys<<<grid, kThreads, 0, st>>>(P->dgraphs, items, cnt, T.tile_words, keys, order);
         BBC_LAUNCH_OK("k_tile_item_keys");
         BBC_TRY(radix_sort_pairs(keys, order, cnt, 16, st));
+        note_launch();
         k_gather_tile_items<<<grid, kThreads, 0, st>>>(items, order, cnt, sorted);
         BBC_LAUNCH_OK("k_gather_tile_items");
         dev_free(keys, st);
         dev_free(order, st);
         dev_free(items, st);
-        if (which == 0)
-            P->pack = sorted;
-        else
-            P->wide = sorted;
+        P->tiles = sorted;
     }
     BBC_CUDA_TRY(cudaStreamSynchronize(st));
     // record the counting step once
     BBC_TRY(configure_count_kernels());
     CountLaunch L{};
     L.graphs = P->dgraphs;
-    L.tile_items = P->pack;
-    L.n_tile_items = P->n_pack;
-    L.wide_items = P->wide;
-    L.n_wide_items = P->n_wide;
+    L.tile_items = P->tiles;
+    L.n_tile_items = P->n_tile;
     L.warp_items = P->warp;
     L.n_warp_items = P->n_warp;
     L.queue = P->queue;
@@ -386,9 +379,10 @@ bbc_status bbc_autotune_batch(int32_t n, bbc_graph *const *gs, bbc_tuning *best,
         struct Cand {
             int tile_words, blocks_per_sm, warp_max;
         };
+        // tile_words 0 = the largest tile for the residency
         const Cand cands[] = {
-            {26624, 2, 256}, {26624, 2, 64}, {26624, 2, 512}, {16384, 2, 256},
-            {8192, 2, 256},  {53248, 1, 256}, {8192, 2, 512},  {4096, 2, 512},
+            {0, 2, 256}, {0, 2, 64}, {0, 2, 512}, {16384, 2, 256},
+            {8192, 2, 256}, {0, 1, 256}, {8192, 2, 512}, {4096, 2, 512},
         };
         std::vector<uint64_t> ref(std::max(n, 1)), got(std::max(n, 1));
         bool have_ref = false;

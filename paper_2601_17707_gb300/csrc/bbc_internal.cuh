@@ -34,13 +34,21 @@ struct DevGraph {
 };
 
 // A unit of work of the tile kernel: anchor `anchor` of graph `graph`, endpoint tiles
-// [tile_begin, tile_end) of width `tile_words` over the anchor's endpoint range.
+// [tile_begin, tile_end) over the anchor's endpoint range. The top two bits of
+// `tile_end_cw` hold the counter width code (0: 8-bit, 1: 16-bit, 2: 32-bit counters),
+// which fixes the endpoints per tile (2, 1 or 1/2 per shared-memory word).
 struct TileItem {
     int32_t graph;
     int32_t anchor;
     int32_t tile_begin;
-    int32_t tile_end;
+    uint32_t tile_end_cw;
 };
+
+__host__ __device__ inline int tile_end_of(const TileItem &t) { return (int)(t.tile_end_cw & 0x3fffffffu); }
+__host__ __device__ inline int tile_width_of(const TileItem &t) { return (int)(t.tile_end_cw >> 30); }
+__host__ __device__ inline uint32_t pack_tile_end(int end, int cw) {
+    return (uint32_t)end | ((uint32_t)cw << 30);
+}
 
 // A unit of work of the hash kernel: one anchor and its oriented wedge count.
 struct HashItem {
@@ -52,9 +60,9 @@ struct HashItem {
 
 // Queue heads and the error word of the persistent kernels; zeroed before a launch.
 struct QueueState {
-    unsigned int tile_head;    // packed-counter tile items
-    unsigned int wide_head;    // 32-bit-counter tile items
+    unsigned int tile_head;    // tile items
     unsigned int warp_head;    // hash items
+    unsigned int spare;
     unsigned int error;        // nonzero: a kernel saw an impossible state (see kErr*)
 };
 
@@ -90,6 +98,18 @@ bbc_status cuda_fail(cudaError_t e, const char *what);
         if (_s != BBC_OK) return _s;                                          \
     } while (0)
 
+// ----------------------------------------------------------------------------- accounting
+
+// Every kernel launch of the library bumps a process-wide counter (bbc_launch_count).
+void note_launch();
+
+// Optional per-kernel timing (bbc_profile_start / bbc_profile_stop): while enabled, the
+// counting kernels are bracketed by CUDA events on their own stream. profile_begin
+// returns a token (-1 when profiling is off or the stream is being captured).
+enum { kProfTile = 0, kProfHash = 1, kProfKinds = 2 };
+int profile_begin(int kind, cudaStream_t st);
+void profile_end(int token, cudaStream_t st);
+
 // ----------------------------------------------------------------------------- memory
 
 // Stream-ordered allocation from the library's own pool on the current device.
@@ -119,24 +139,23 @@ bbc_status exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, cuda
 
 struct CountLaunch {
     const DevGraph *graphs;     // device array
-    const TileItem *tile_items; // device, packed 16-bit counters
+    const TileItem *tile_items; // device
     int32_t n_tile_items;
-    const TileItem *wide_items; // device, 32-bit counters
-    int32_t n_wide_items;
     const HashItem *warp_items; // device
     int32_t n_warp_items;
     QueueState *queue;          // device, zeroed by the caller before the launch
     Tuning tuning;
 };
 
-// Queues the counting kernels (packed tiles, wide tiles, warp hash) on `st`.
+// Queues the counting kernels (dense tiles, then warp hash) on `st`.
 bbc_status launch_count(const CountLaunch &L, cudaStream_t st);
 
 // Sets the kernels' shared-memory limits on the current device (idempotent); done
 // before any stream capture so that capture only records launches.
 bbc_status configure_count_kernels();
 
-int tile_kernel_smem_bytes(int tile_words, bool wide);
+// Static shared memory of the tile kernel (its dynamic part is the counter tile).
+int tile_static_smem_bytes();
 
 // Splits anchors whose wedge count exceeds a fair share of one block's work.
 long long auto_split(uint64_t wedges, int sm_count, int blocks_per_sm);

@@ -32,7 +32,10 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kTileThreads = 512;
 constexpr int kTileWarps = kTileThreads / 32;
-constexpr int kLongSlice = 64;            // slices this long are swept by a whole warp
+constexpr int kChunk = kTileThreads;      // centres per block-sweep chunk
+constexpr int kLongMin = 256;             // slices this long are cut into pieces
+constexpr int kPiece = 1024;              // wedges per piece of a long slice
+constexpr int kLongSlice = 64;            // warp sweep: slices this long use the whole warp
 constexpr int kHashThreads = 256;
 constexpr int kHashWarps = kHashThreads / 32;
 constexpr int kHashSlots = 1024;          // per warp; holds anchors of <= 512 wedges
@@ -61,25 +64,6 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
 }
 
 // ----------------------------------------------------------------------------- counters
-
-// Dense tile over endpoint ranks [lo, lo + width).
-template <bool WIDE>
-struct TileCounter {
-    uint32_t *tile;
-    uint32_t lo;
-    __device__ __forceinline__ void bump(uint32_t w, uint32_t t) const {
-        const uint32_t i = w - lo;
-        if (WIDE)
-            atomicAdd(tile + 2 * i + t, 1u);
-        else
-            atomicAdd(tile + i, 1u << (t << 4));
-    }
-    __device__ __forceinline__ uint32_t peek(uint32_t w, uint32_t t) const {
-        const uint32_t i = w - lo;
-        if (WIDE) return tile[2 * i + t];
-        return (tile[i] >> (t << 4)) & 0xffffu;
-    }
-};
 
 // Open addressing (linear probing) over `mask + 1` slots; values are packed p | n << 16.
 // The table is sized to at least twice the anchor's wedge count, so it never fills; the
@@ -126,12 +110,12 @@ struct HashCounter {
 
 // ----------------------------------------------------------------------------- sweep
 
-// One pass over the oriented wedges of anchor rows [sb, se) whose endpoints lie in
-// [lo, hi). MODE 0 bumps the counters; MODE 1 (the per-vertex centre pass) reads them
-// and adds (count - 1) per wedge to the centre's b. Warps take batches of 32 centres
-// from *batch_ctr; lane j of a batch owns centre j and its slice.
+// One warp's pass over the oriented wedges of anchor rows [sb, se) whose endpoints lie
+// in [lo, hi) (the hash kernel's sweep). MODE 0 bumps the counters; MODE 1 (the
+// per-vertex centre pass) reads them and adds (count - 1) per wedge to the centre's b.
+// The warp takes batches of 32 centres from *batch_ctr; lane j owns centre j's slice.
 template <int MODE, class Counter>
-__device__ __forceinline__ void sweep(const DevGraph &G, int64_t sb, int64_t se, uint32_t lo,
+__device__ __forceinline__ void warp_sweep(const DevGraph &G, int64_t sb, int64_t se, uint32_t lo,
                                       uint32_t hi, const Counter &ctr, int *batch_ctr,
                                       uint32_t *sacc) {
     const int lane = threadIdx.x & 31;
@@ -220,64 +204,284 @@ __device__ __forceinline__ void sweep(const DevGraph &G, int64_t sb, int64_t se,
     }
 }
 
-// Reads, reduces and clears the tile of endpoints [lo, hi).
-template <bool WIDE>
-__device__ __forceinline__ void tile_epilogue(uint32_t *tile, uint32_t lo, uint32_t hi,
-                                              unsigned long long *bS, unsigned long long &bal,
-                                              unsigned long long &unb) {
-    const int n = (int)(hi - lo);
-    if (!WIDE) {
-        uint4 *t4 = reinterpret_cast<uint4 *>(tile);
-        const int n4 = (n + 3) >> 2;  // the tail words beyond n are always zero
-        for (int i = threadIdx.x; i < n4; i += blockDim.x) {
-            const uint4 q = t4[i];
-            if ((q.x | q.y | q.z | q.w) == 0) continue;
-            const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+// ----------------------------------------------------------------------------- tiles
+
+// Dense counters over the endpoint ranks [lo, lo + endpoints) of one tile. The counter
+// width follows the largest count the anchor can reach (its degree, or its wedge count
+// if smaller): CW 0 packs two endpoints of two 8-bit counters (p, n) per word, CW 1 one
+// endpoint of two 16-bit counters, CW 2 one endpoint of two 32-bit words.
+template <int CW>
+struct TileCounter {
+    uint32_t *tile;
+    uint32_t lo;
+    static constexpr int kPerWord2 = CW == 0 ? 4 : (CW == 1 ? 2 : 1);  // endpoints per 2 words
+    __device__ __forceinline__ void bump(uint32_t w, uint32_t t) const {
+        const uint32_t e = w - lo;
+        if (CW == 0)
+            atomicAdd(tile + (e >> 1), 1u << (((e & 1u) << 4) | (t << 3)));
+        else if (CW == 1)
+            atomicAdd(tile + e, 1u << (t << 4));
+        else
+            atomicAdd(tile + 2 * e + t, 1u);
+    }
+    __device__ __forceinline__ uint32_t peek(uint32_t w, uint32_t t) const {
+        const uint32_t e = w - lo;
+        if (CW == 0) return (tile[e >> 1] >> (((e & 1u) << 4) | (t << 3))) & 0xffu;
+        if (CW == 1) return (tile[e] >> (t << 4)) & 0xffffu;
+        return tile[2 * e + t];
+    }
+};
+
+__host__ __device__ constexpr uint32_t endpoints_per_tile(int cw, uint32_t tile_words) {
+    return cw == 0 ? tile_words * 2 : (cw == 1 ? tile_words : tile_words / 2);
+}
+
+// Per-chunk bookkeeping of the block sweep: the slice of every centre of the chunk and
+// two prefix sums, over short-slice wedges and over long-slice pieces.
+struct ChunkSmem {
+    uint32_t start[kChunk];
+    uint32_t len[kChunk];
+    uint32_t ent[kChunk];
+    uint32_t pshort[kChunk + 1];
+    uint32_t ppiece[kChunk + 1];
+    unsigned long long acc[kChunk];
+    unsigned long long wsum[kTileWarps];
+    int piece_ctr;
+};
+
+__device__ __forceinline__ unsigned long long block_exclusive_scan_u64(unsigned long long x,
+                                                                      unsigned long long *total,
+                                                                      unsigned long long *wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long inc = x;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const unsigned long long p = w4[k] & 0xffffu, m = w4[k] >> 16;
-                const unsigned long long f = choose2(p) + choose2(m);
-                bal += f;
-                unb += p * m;
-                if (bS && f) atomicAdd(bS + lo + 4 * i + k, f);
-            }
-            t4[i] = make_uint4(0, 0, 0, 0);
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned long long w = lane < kTileWarps ? wsum[lane] : 0ull;
+        unsigned long long wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, wi, o);
+            if (lane >= o) wi += y;
         }
-    } else {
-        uint4 *t4 = reinterpret_cast<uint4 *>(tile);
-        const int n2 = (n + 1) >> 1;  // two endpoints per 16 bytes
-        for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-            const uint4 q = t4[i];
-            if ((q.x | q.y | q.z | q.w) == 0) continue;
-            const unsigned long long p0 = q.x, m0 = q.y, p1 = q.z, m1 = q.w;
-            const unsigned long long f0 = choose2(p0) + choose2(m0);
-            const unsigned long long f1 = choose2(p1) + choose2(m1);
-            bal += f0 + f1;
-            unb += p0 * m0 + p1 * m1;
-            if (bS) {
-                if (f0) atomicAdd(bS + lo + 2 * i, f0);
-                if (f1) atomicAdd(bS + lo + 2 * i + 1, f1);
-            }
-            t4[i] = make_uint4(0, 0, 0, 0);
+        if (lane < kTileWarps) wsum[lane] = wi - w;
+        if (lane == kTileWarps - 1) *total = wi;
+    }
+    __syncthreads();
+    return wsum[warp] + inc - x;
+}
+
+// index of the last entry <= k in the non-decreasing p[0..kChunk] (p[0] == 0 <= k)
+__device__ __forceinline__ int last_le(const uint32_t *p, uint32_t k) {
+    int lo = 0, hi = kChunk;  // invariant: p[lo] <= k < p[hi + 1] or hi == kChunk
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p[mid] <= k)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int MODE, int CW>
+__device__ __forceinline__ void wedge(const TileCounter<CW> &ctr, uint32_t x, uint32_t sg,
+                                      unsigned long long &acc) {
+    const uint32_t t = (x ^ sg) >> 31;
+    if (MODE == 0)
+        ctr.bump(x & kIdMask, t);
+    else
+        acc += ctr.peek(x & kIdMask, t) - 1u;
+}
+
+// One pass of the whole block over the oriented wedges of anchor rows [sb, se) whose
+// endpoints lie in [lo, hi), in chunks of kChunk centres. Per chunk, every thread finds
+// its centre's slice (binary search in the rank-sorted C -> S row); slices shorter than
+// kLongMin are concatenated and cut into equal contiguous shares, one per thread; longer
+// ones are cut into kPiece-wedge pieces that warps pull from a shared counter and sweep
+// with coalesced 16-byte loads. MODE 0 bumps the counters; MODE 1 reads them and adds
+// (count - 1) per wedge to the centre's per-vertex sum.
+template <int MODE, int CW>
+__device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, uint32_t lo, uint32_t hi,
+                            const TileCounter<CW> &ctr, ChunkSmem &cs) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint32_t *__restrict__ rowC = G.rowC;
+    for (int64_t cb = sb; cb < se; cb += kChunk) {
+        const int64_t ci = cb + tid;
+        uint32_t start = 0, len = 0, ent = 0;
+        if (ci < se) {
+            ent = __ldg(G.rowS + ci);
+            const uint32_t c = ent & kIdMask;
+            const int64_t rb = __ldg(G.rowC_off + c), re = __ldg(G.rowC_off + c + 1);
+            const int64_t b = lo == 0 ? rb : lower_bound_rank(rowC, rb, re, lo);
+            const int64_t e = hi >= (uint32_t)G.nS ? re : lower_bound_rank(rowC, b, re, hi);
+            start = (uint32_t)b;
+            len = (uint32_t)(e - b);
         }
+        const bool islong = len >= (uint32_t)kLongMin;
+        const unsigned long long mine =
+            ((unsigned long long)(islong ? (len + kPiece - 1) / kPiece : 0u) << 32) |
+            (islong ? 0u : len);
+        unsigned long long total;
+        __shared__ unsigned long long s_total;
+        const unsigned long long ex = block_exclusive_scan_u64(mine, &s_total, cs.wsum);
+        cs.start[tid] = start;
+        cs.len[tid] = len;
+        cs.ent[tid] = ent;
+        cs.pshort[tid] = (uint32_t)ex;
+        cs.ppiece[tid] = (uint32_t)(ex >> 32);
+        if (MODE == 1) cs.acc[tid] = 0;
+        if (tid == 0) cs.piece_ctr = 0;
+        total = s_total;
+        if (tid == kChunk - 1) {
+            cs.pshort[kChunk] = (uint32_t)total;
+            cs.ppiece[kChunk] = (uint32_t)(total >> 32);
+        }
+        __syncthreads();
+        const uint32_t NS = (uint32_t)total, NP = (uint32_t)(total >> 32);
+        // short slices: contiguous equal shares
+        if (NS) {
+            uint32_t k = (uint32_t)(((unsigned long long)NS * tid) / kChunk);
+            const uint32_t k1 = (uint32_t)(((unsigned long long)NS * (tid + 1)) / kChunk);
+            if (k < k1) {
+                int j = last_le(cs.pshort, k);
+                uint32_t nb = cs.pshort[j + 1];
+                uint32_t base = cs.start[j] - cs.pshort[j];
+                uint32_t sg = cs.ent[j] & kSignBit;
+                unsigned long long acc = 0;
+                for (; k < k1; ++k) {
+                    if (k >= nb) {
+                        if (MODE == 1 && acc) {
+                            atomicAdd(cs.acc + j, acc);
+                            acc = 0;
+                        }
+                        do {
+                            ++j;
+                            nb = cs.pshort[j + 1];
+                        } while (nb <= k);
+                        base = cs.start[j] - cs.pshort[j];
+                        sg = cs.ent[j] & kSignBit;
+                    }
+                    wedge<MODE>(ctr, __ldg(rowC + (uint32_t)(base + k)), sg, acc);
+                }
+                if (MODE == 1 && acc) atomicAdd(cs.acc + j, acc);
+            }
+        }
+        // long slices: pieces pulled by warps
+        if (NP) {
+            for (;;) {
+                uint32_t pc = 0;
+                if (lane == 0) pc = (uint32_t)atomicAdd(&cs.piece_ctr, 1);
+                pc = __shfl_sync(kFull, pc, 0);
+                if (pc >= NP) break;
+                const int j = last_le(cs.ppiece, pc);
+                const uint32_t off = (pc - cs.ppiece[j]) * (uint32_t)kPiece;
+                const uint32_t n = min((uint32_t)kPiece, cs.len[j] - off);
+                const uint32_t s = cs.start[j] + off;
+                const uint32_t sg = cs.ent[j] & kSignBit;
+                unsigned long long acc = 0;
+                const uint32_t head = min(n, (4u - (s & 3u)) & 3u);
+                if ((uint32_t)lane < head) wedge<MODE>(ctr, __ldg(rowC + s + lane), sg, acc);
+                const uint32_t m4 = (n - head) >> 2;
+                const uint4 *v4 = reinterpret_cast<const uint4 *>(rowC + s + head);
+                for (uint32_t q = lane; q < m4; q += 32) {
+                    const uint4 x = __ldg(v4 + q);
+                    wedge<MODE>(ctr, x.x, sg, acc);
+                    wedge<MODE>(ctr, x.y, sg, acc);
+                    wedge<MODE>(ctr, x.z, sg, acc);
+                    wedge<MODE>(ctr, x.w, sg, acc);
+                }
+                const uint32_t rest = (n - head) & 3u;
+                if ((uint32_t)lane < rest) wedge<MODE>(ctr, __ldg(rowC + s + head + 4 * m4 + lane), sg, acc);
+                if (MODE == 1) {
+                    acc = warp_sum(acc);
+                    if (lane == 0 && acc) atomicAdd(cs.acc + j, acc);
+                }
+            }
+        }
+        __syncthreads();
+        if (MODE == 1 && ci < se && cs.acc[tid]) atomicAdd(G.bC + (ent & kIdMask), cs.acc[tid]);
     }
 }
 
-// ----------------------------------------------------------------------------- kernels
+__device__ __forceinline__ void pair_total(unsigned long long p, unsigned long long m,
+                                           unsigned long long *bS, uint32_t w,
+                                           unsigned long long &bal, unsigned long long &unb) {
+    const unsigned long long f = choose2(p) + choose2(m);
+    bal += f;
+    unb += p * m;
+    if (bS && f) atomicAdd(bS + w, f);
+}
 
-template <bool WIDE>
+// Reads, reduces and clears the tile of endpoints [lo, hi). Words past the last
+// endpoint in the final 16-byte group are never bumped and stay zero.
+template <int CW>
+__device__ __forceinline__ void tile_epilogue(uint32_t *tile, uint32_t lo, uint32_t hi,
+                                              unsigned long long *bS, unsigned long long &bal,
+                                              unsigned long long &unb) {
+    const uint32_t n = hi - lo;
+    const uint32_t words = CW == 0 ? (n + 1) / 2 : (CW == 1 ? n : 2 * n);
+    const uint32_t n4 = (words + 3) / 4;
+    uint4 *t4 = reinterpret_cast<uint4 *>(tile);
+    for (uint32_t i = threadIdx.x; i < n4; i += blockDim.x) {
+        const uint4 q = t4[i];
+        if ((q.x | q.y | q.z | q.w) == 0) continue;
+        if (CW == 0) {
+            const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t e = lo + 8 * i + 2 * k;
+                pair_total(w4[k] & 0xffu, (w4[k] >> 8) & 0xffu, bS, e, bal, unb);
+                pair_total((w4[k] >> 16) & 0xffu, w4[k] >> 24, bS, e + 1, bal, unb);
+            }
+        } else if (CW == 1) {
+            const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) pair_total(w4[k] & 0xffffu, w4[k] >> 16, bS, lo + 4 * i + k, bal, unb);
+        } else {
+            pair_total(q.x, q.y, bS, lo + 2 * i, bal, unb);
+            pair_total(q.z, q.w, bS, lo + 2 * i + 1, bal, unb);
+        }
+        t4[i] = make_uint4(0, 0, 0, 0);
+    }
+}
+
+template <int CW>
+__device__ void run_tile_item(const DevGraph &G, const TileItem &item, int tile_words, uint32_t *tile,
+                              ChunkSmem &cs, unsigned long long &bal, unsigned long long &unb) {
+    const int a = item.anchor;
+    const int64_t sb = G.rowS_off[a], se = G.rowS_off[a + 1];
+    const uint32_t ept = endpoints_per_tile(CW, (uint32_t)tile_words);
+    const uint32_t range_lo = G.orient_low ? 0u : (uint32_t)a + 1u;
+    const uint32_t range_hi = G.orient_low ? (uint32_t)a : (uint32_t)G.nS;
+    const int t1 = tile_end_of(item);
+    for (int t = item.tile_begin; t < t1; ++t) {
+        const uint32_t lo = range_lo + (uint32_t)t * ept;
+        const uint32_t hi = min(lo + ept, range_hi);
+        const TileCounter<CW> ctr{tile, lo};
+        block_sweep<0>(G, sb, se, lo, hi, ctr, cs);
+        if (G.bC) block_sweep<1>(G, sb, se, lo, hi, ctr, cs);
+        tile_epilogue<CW>(tile, lo, hi, G.bS, bal, unb);
+        __syncthreads();
+    }
+}
+
+// Persistent blocks pop (anchor, tile range) items, heaviest first.
 __global__ void __launch_bounds__(kTileThreads, 2)
 k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, int n_items,
        unsigned *head, int tile_words) {
     extern __shared__ uint4 smem_tile[];
     uint32_t *tile = reinterpret_cast<uint32_t *>(smem_tile);
+    __shared__ ChunkSmem cs;
     __shared__ int s_item;
-    __shared__ int s_batch[2];
-    __shared__ uint32_t s_acc[kTileWarps][32];
     __shared__ unsigned long long s_red[2][kTileWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < tile_words; i += blockDim.x) tile[i] = 0;
-    const uint32_t ept = WIDE ? (uint32_t)tile_words / 2 : (uint32_t)tile_words;
     for (;;) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
         __syncthreads();
@@ -285,28 +489,11 @@ k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, 
         if (it >= n_items) break;
         const TileItem item = items[it];
         const DevGraph &G = graphs[item.graph];
-        const int a = item.anchor;
-        const int64_t sb = G.rowS_off[a], se = G.rowS_off[a + 1];
-        const uint32_t range_lo = G.orient_low ? 0u : (uint32_t)a + 1u;
-        const uint32_t range_hi = G.orient_low ? (uint32_t)a : (uint32_t)G.nS;
         unsigned long long bal = 0, unb = 0;
-        for (int t = item.tile_begin; t < item.tile_end; ++t) {
-            const uint32_t lo = range_lo + (uint32_t)t * ept;
-            const uint32_t hi = min(lo + ept, range_hi);
-            if (threadIdx.x == 0) {
-                s_batch[0] = 0;
-                s_batch[1] = 0;
-            }
-            __syncthreads();
-            const TileCounter<WIDE> ctr{tile, lo};
-            sweep<0>(G, sb, se, lo, hi, ctr, &s_batch[0], nullptr);
-            __syncthreads();
-            if (G.bC) {
-                sweep<1>(G, sb, se, lo, hi, ctr, &s_batch[1], s_acc[warp]);
-                __syncthreads();
-            }
-            tile_epilogue<WIDE>(tile, lo, hi, G.bS, bal, unb);
-            __syncthreads();
+        switch (tile_width_of(item)) {
+            case 0: run_tile_item<0>(G, item, tile_words, tile, cs, bal, unb); break;
+            case 1: run_tile_item<1>(G, item, tile_words, tile, cs, bal, unb); break;
+            default: run_tile_item<2>(G, item, tile_words, tile, cs, bal, unb); break;
         }
         bal = warp_sum(bal);
         unb = warp_sum(unb);
@@ -323,7 +510,7 @@ k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, 
             }
             if (B) atomicAdd(G.totals + 0, B);
             if (U) atomicAdd(G.totals + 1, U);
-            if (G.bS && B) atomicAdd(G.bS + a, B);
+            if (G.bS && B) atomicAdd(G.bS + item.anchor, B);
         }
     }
 }
@@ -359,12 +546,12 @@ k_warp_hash(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ it
         const HashCounter ctr{keys, vals, (1u << lg) - 1u, 32 - lg, &q->error};
         if (lane == 0) s_batch[warp] = 0;
         __syncwarp();
-        sweep<0>(G, sb, se, lo, hi, ctr, &s_batch[warp], nullptr);
+        warp_sweep<0>(G, sb, se, lo, hi, ctr, &s_batch[warp], nullptr);
         __syncwarp();
         if (G.bC) {
             if (lane == 0) s_batch[warp] = 0;
             __syncwarp();
-            sweep<1>(G, sb, se, lo, hi, ctr, &s_batch[warp], s_acc[warp]);
+            warp_sweep<1>(G, sb, se, lo, hi, ctr, &s_batch[warp], s_acc[warp]);
             __syncwarp();
         }
         unsigned long long bal = 0, unb = 0;
@@ -393,19 +580,21 @@ k_warp_hash(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ it
 
 }  // namespace
 
-int tile_kernel_smem_bytes(int tile_words, bool) { return tile_words * 4; }
-
 bbc_status configure_count_kernels() {
     static thread_local int configured_device = -1;
     int dev = 0;
     BBC_CUDA_TRY(cudaGetDevice(&dev));
     if (configured_device != dev) {
+        cudaFuncAttributes fa{};
+        BBC_CUDA_TRY(cudaFuncGetAttributes(&fa, k_tile));
+        if ((int)fa.sharedSizeBytes > tile_static_smem_bytes()) {
+            set_error("tile kernel static shared memory exceeds its budget");
+            return BBC_E_CUDA;
+        }
         int maxopt = 0;
         BBC_CUDA_TRY(cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        BBC_CUDA_TRY(cudaFuncSetAttribute(k_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          maxopt - 4096));
-        BBC_CUDA_TRY(cudaFuncSetAttribute(k_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          maxopt - 4096));
+        BBC_CUDA_TRY(cudaFuncSetAttribute(k_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          maxopt - (int)fa.sharedSizeBytes));
         BBC_CUDA_TRY(cudaFuncSetAttribute(k_warp_hash, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           kHashWarps * 2 * kHashSlots * 4));
         configured_device = dev;
@@ -417,26 +606,27 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
     BBC_TRY(configure_count_kernels());
     const int sms = device_sm_count();
     const Tuning &T = L.tuning;
-    const size_t tile_smem = (size_t)T.tile_words * 4;
     if (L.n_tile_items > 0) {
-        const int grid = sms * T.blocks_per_sm;
-        k_tile<false><<<grid, kTileThreads, tile_smem, st>>>(L.graphs, L.tile_items, L.n_tile_items,
-                                                             &L.queue->tile_head, T.tile_words);
+        const int tok = profile_begin(kProfTile, st);
+        note_launch();
+        k_tile<<<sms * T.blocks_per_sm, kTileThreads, (size_t)T.tile_words * 4, st>>>(
+            L.graphs, L.tile_items, L.n_tile_items, &L.queue->tile_head, T.tile_words);
         BBC_CUDA_TRY(cudaGetLastError());
-    }
-    if (L.n_wide_items > 0) {
-        const int grid = sms * T.blocks_per_sm;
-        k_tile<true><<<grid, kTileThreads, tile_smem, st>>>(L.graphs, L.wide_items, L.n_wide_items,
-                                                            &L.queue->wide_head, T.tile_words);
-        BBC_CUDA_TRY(cudaGetLastError());
+        profile_end(tok, st);
     }
     if (L.n_warp_items > 0) {
-        const int grid = sms * 3;
-        k_warp_hash<<<grid, kHashThreads, kHashWarps * 2 * kHashSlots * 4, st>>>(
+        const int tok = profile_begin(kProfHash, st);
+        note_launch();
+        k_warp_hash<<<sms * 3, kHashThreads, kHashWarps * 2 * kHashSlots * 4, st>>>(
             L.graphs, L.warp_items, L.n_warp_items, L.queue);
         BBC_CUDA_TRY(cudaGetLastError());
+        profile_end(tok, st);
     }
     return BBC_OK;
 }
+
+// An upper bound of the tile kernel's static shared memory (checked against the
+// compiled kernel when the kernels are configured).
+int tile_static_smem_bytes() { return (int)sizeof(ChunkSmem) + 512; }
 
 }  // namespace bbc

@@ -27,10 +27,8 @@ struct bbc_graph {
     // work lists (rebuilt when the tuning changes)
     bbc::Tuning items_tuning{};
     bool items_valid = false;
-    bbc::TileItem *tile_pack = nullptr;
-    int32_t n_tile_pack = 0;
-    bbc::TileItem *tile_wide = nullptr;
-    int32_t n_tile_wide = 0;
+    bbc::TileItem *tile_items = nullptr;
+    int32_t n_tile = 0;
     bbc::HashItem *warp_items = nullptr;
     int32_t n_warp = 0;
 

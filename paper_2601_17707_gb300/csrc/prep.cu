@@ -228,10 +228,14 @@ struct ClassifyParams {
     long long split;
 };
 
+// Work of one anchor: kind 0 none, 1 warp-hash item, 2 tile items; for tiles, the
+// counter width code (largest reachable count min(degree, wedges) <= 255 / 65535 / more),
+// the number of tiles over its endpoint range and how many items they are split into.
 __device__ __forceinline__ void classify_one(const ClassifyParams &P, unsigned long long wl,
-                                             int64_t deg, int a, int *kind, int *ntiles,
+                                             int64_t deg, int a, int *kind, int *cw, int *ntiles,
                                              int *groups) {
     *kind = 0;
+    *cw = 0;
     *ntiles = 0;
     *groups = 0;
     if (wl == 0 || deg < 2) return;
@@ -240,28 +244,27 @@ __device__ __forceinline__ void classify_one(const ClassifyParams &P, unsigned l
         return;
     }
     const long long maxcount = deg < (long long)wl ? deg : (long long)wl;
-    const bool wide = maxcount > 65535;
-    const int ept = wide ? P.tile_words / 2 : P.tile_words;
+    const int w = maxcount <= 255 ? 0 : (maxcount <= 65535 ? 1 : 2);
+    const long long ept = w == 0 ? 2ll * P.tile_words : (w == 1 ? P.tile_words : P.tile_words / 2);
     const long long span = P.orient_low ? a : (long long)P.nS - 1 - a;
     const int nt = (int)((span + ept - 1) / ept);
     long long g = 1;
     if ((long long)wl > P.split) g = ((long long)wl + P.split - 1) / P.split;
     if (g > nt) g = nt;
-    *kind = wide ? 3 : 2;
+    *kind = 2;
+    *cw = w;
     *ntiles = nt;
     *groups = (int)g;
 }
 
-// Per anchor: how many packed-tile items, wide-tile items and warp items it yields.
 __global__ void k_classify(ClassifyParams P, const unsigned long long *__restrict__ wl,
-                           const int64_t *__restrict__ rowS_off, int32_t *__restrict__ n_pack,
-                           int32_t *__restrict__ n_wide, int32_t *__restrict__ n_warp) {
+                           const int64_t *__restrict__ rowS_off, int32_t *__restrict__ n_tile,
+                           int32_t *__restrict__ n_warp) {
     for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < P.nS;
          a += (int64_t)gridDim.x * blockDim.x) {
-        int kind, nt, g;
-        classify_one(P, wl[a], rowS_off[a + 1] - rowS_off[a], (int)a, &kind, &nt, &g);
-        n_pack[a] = kind == 2 ? g : 0;
-        n_wide[a] = kind == 3 ? g : 0;
+        int kind, cw, nt, g;
+        classify_one(P, wl[a], rowS_off[a + 1] - rowS_off[a], (int)a, &kind, &cw, &nt, &g);
+        n_tile[a] = kind == 2 ? g : 0;
         n_warp[a] = kind == 1 ? 1 : 0;
     }
 }
@@ -269,25 +272,23 @@ __global__ void k_classify(ClassifyParams P, const unsigned long long *__restric
 // Writes the items and, per tile item, a 16-bit sort key that orders items by their
 // expected wedge count, largest first (the fanout ordering of Algorithm 4).
 __global__ void k_emit_items(ClassifyParams P, const unsigned long long *__restrict__ wl,
-                             const int64_t *__restrict__ rowS_off, const int64_t *__restrict__ pos_pack,
-                             const int64_t *__restrict__ pos_wide, const int64_t *__restrict__ pos_warp,
-                             TileItem *__restrict__ pack, uint32_t *__restrict__ key_pack,
-                             TileItem *__restrict__ wide, uint32_t *__restrict__ key_wide,
-                             HashItem *__restrict__ warp) {
+                             const int64_t *__restrict__ rowS_off, const int64_t *__restrict__ pos_tile,
+                             const int64_t *__restrict__ pos_warp, TileItem *__restrict__ tiles,
+                             uint32_t *__restrict__ keys, HashItem *__restrict__ warp) {
     for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < P.nS;
          a += (int64_t)gridDim.x * blockDim.x) {
-        int kind, nt, g;
+        int kind, cw, nt, g;
         const unsigned long long w = wl[a];
-        classify_one(P, w, rowS_off[a + 1] - rowS_off[a], (int)a, &kind, &nt, &g);
+        classify_one(P, w, rowS_off[a + 1] - rowS_off[a], (int)a, &kind, &cw, &nt, &g);
         if (kind == 1) {
             warp[pos_warp[a]] = HashItem{0, (int32_t)a, (int32_t)w, 0};
-        } else if (kind >= 2) {
-            TileItem *dst = kind == 2 ? pack + pos_pack[a] : wide + pos_wide[a];
-            uint32_t *kd = kind == 2 ? key_pack + pos_pack[a] : key_wide + pos_wide[a];
+        } else if (kind == 2) {
+            TileItem *dst = tiles + pos_tile[a];
+            uint32_t *kd = keys + pos_tile[a];
             for (int i = 0; i < g; ++i) {
                 const int t0 = (int)((long long)nt * i / g);
                 const int t1 = (int)((long long)nt * (i + 1) / g);
-                dst[i] = TileItem{0, (int32_t)a, t0, t1};
+                dst[i] = TileItem{0, (int32_t)a, t0, pack_tile_end(t1, cw)};
                 const double cost = (double)w * (double)(t1 - t0) / (double)nt + 1.0;
                 int q = (int)(log2(cost) * 1024.0);
                 q = q < 0 ? 0 : (q > 65535 ? 65535 : q);
@@ -343,9 +344,11 @@ bbc_status rank_side(const int32_t *deg, int64_t n, int32_t maxdeg, int32_t *ran
     uint32_t *k = nullptr, *vv = nullptr;
     BBC_TRY(sc.get(&k, (size_t)n));
     BBC_TRY(sc.get(&vv, (size_t)n));
+    note_launch();
     k_rank_keys<<<grid_for(n), kThreads, 0, st>>>(deg, n, maxdeg, k, vv);
     BBC_LAUNCH_CHECK("k_rank_keys");
     BBC_TRY(radix_sort_pairs(k, vv, n, bit_length((uint64_t)maxdeg), st));
+    note_launch();
     k_invert_perm<<<grid_for(n), kThreads, 0, st>>>(vv, n, rank, perm);
     BBC_LAUNCH_CHECK("k_invert_perm");
     return BBC_OK;
@@ -372,7 +375,7 @@ DevGraph host_descriptor(const bbc_graph *g, bool per_vertex) {
 void release_graph(bbc_graph *g, cudaStream_t st) {
     if (!g) return;
     void *ptrs[] = {g->rowS_off, g->rowS, g->rowC_off, g->rowC, g->permS, g->permC, g->wl,
-                    g->tile_pack, g->tile_wide, g->warp_items, g->dgraph, g->bS, g->bC,
+                    g->tile_items, g->warp_items, g->dgraph, g->bS, g->bC,
                     g->totals, g->queue};
     for (void *p : ptrs)
         if (p) dev_free(p, st);
@@ -384,12 +387,11 @@ bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
         g->items_tuning.warp_max_wedges == t.warp_max_wedges &&
         g->items_tuning.split_wedges == t.split_wedges)
         return BBC_OK;
-    if (g->tile_pack) dev_free(g->tile_pack, st);
-    if (g->tile_wide) dev_free(g->tile_wide, st);
+    if (g->tile_items) dev_free(g->tile_items, st);
     if (g->warp_items) dev_free(g->warp_items, st);
-    g->tile_pack = g->tile_wide = nullptr;
+    g->tile_items = nullptr;
     g->warp_items = nullptr;
-    g->n_tile_pack = g->n_tile_wide = g->n_warp = 0;
+    g->n_tile = g->n_warp = 0;
     g->items_valid = false;
     const int64_t nS = g->nS;
     if (nS == 0) {
@@ -398,63 +400,49 @@ bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
         return BBC_OK;
     }
     Scratch sc(st);
-    int32_t *np = nullptr, *nw = nullptr, *nh = nullptr;
-    int64_t *pp = nullptr, *pw = nullptr, *ph = nullptr;
-    BBC_TRY(sc.get(&np, (size_t)nS));
-    BBC_TRY(sc.get(&nw, (size_t)nS));
+    int32_t *nt = nullptr, *nh = nullptr;
+    int64_t *pt = nullptr, *ph = nullptr;
+    BBC_TRY(sc.get(&nt, (size_t)nS));
     BBC_TRY(sc.get(&nh, (size_t)nS));
-    BBC_TRY(sc.get(&pp, (size_t)nS + 1));
-    BBC_TRY(sc.get(&pw, (size_t)nS + 1));
+    BBC_TRY(sc.get(&pt, (size_t)nS + 1));
     BBC_TRY(sc.get(&ph, (size_t)nS + 1));
     ClassifyParams P{g->nS, g->orient_low, t.tile_words, t.warp_max_wedges, t.split_wedges};
-    k_classify<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, np, nw, nh);
+    note_launch();
+    k_classify<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, nt, nh);
     BBC_LAUNCH_CHECK("k_classify");
-    BBC_TRY(exclusive_scan_i32_to_i64(np, pp, nS, st));
-    BBC_TRY(exclusive_scan_i32_to_i64(nw, pw, nS, st));
+    BBC_TRY(exclusive_scan_i32_to_i64(nt, pt, nS, st));
     BBC_TRY(exclusive_scan_i32_to_i64(nh, ph, nS, st));
-    int64_t counts[3];
-    BBC_CUDA_TRY(cudaMemcpyAsync(&counts[0], pp + nS, 8, cudaMemcpyDeviceToHost, st));
-    BBC_CUDA_TRY(cudaMemcpyAsync(&counts[1], pw + nS, 8, cudaMemcpyDeviceToHost, st));
-    BBC_CUDA_TRY(cudaMemcpyAsync(&counts[2], ph + nS, 8, cudaMemcpyDeviceToHost, st));
+    int64_t counts[2];
+    BBC_CUDA_TRY(cudaMemcpyAsync(&counts[0], pt + nS, 8, cudaMemcpyDeviceToHost, st));
+    BBC_CUDA_TRY(cudaMemcpyAsync(&counts[1], ph + nS, 8, cudaMemcpyDeviceToHost, st));
     BBC_CUDA_TRY(cudaStreamSynchronize(st));
-    if (counts[0] > INT32_MAX || counts[1] > INT32_MAX || counts[2] > INT32_MAX) {
+    if (counts[0] > INT32_MAX || counts[1] > INT32_MAX) {
         set_error("work list longer than 2^31 items");
         return BBC_E_INVALID_ARG;
     }
-    TileItem *pack = nullptr, *wide = nullptr;
-    uint32_t *kp = nullptr, *kw = nullptr;
-    HashItem *warp = nullptr;
-    BBC_TRY(sc.get(&pack, (size_t)counts[0]));
-    BBC_TRY(sc.get(&kp, (size_t)counts[0]));
-    BBC_TRY(sc.get(&wide, (size_t)counts[1]));
-    BBC_TRY(sc.get(&kw, (size_t)counts[1]));
-    BBC_TRY(dev_alloc_n(&warp, (size_t)counts[2], st));
-    g->warp_items = warp;
-    g->n_warp = (int32_t)counts[2];
-    k_emit_items<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, pp, pw, ph, pack, kp,
-                                                     wide, kw, warp);
+    const int64_t ntile = counts[0];
+    TileItem *raw = nullptr;
+    uint32_t *keys = nullptr;
+    BBC_TRY(sc.get(&raw, (size_t)ntile));
+    BBC_TRY(sc.get(&keys, (size_t)ntile));
+    BBC_TRY(dev_alloc_n(&g->warp_items, (size_t)counts[1], st));
+    g->n_warp = (int32_t)counts[1];
+    BBC_TRY(dev_alloc_n(&g->tile_items, (size_t)ntile, st));
+    g->n_tile = (int32_t)ntile;
+    note_launch();
+    k_emit_items<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, pt, ph, raw, keys,
+                                                     g->warp_items);
     BBC_LAUNCH_CHECK("k_emit_items");
     // Order the tile items by expected cost, largest first.
-    for (int which = 0; which < 2; ++which) {
-        const int64_t n = counts[which];
-        TileItem *src = which == 0 ? pack : wide;
-        uint32_t *keys = which == 0 ? kp : kw;
-        TileItem *dst = nullptr;
-        BBC_TRY(dev_alloc_n(&dst, (size_t)n, st));
-        if (which == 0) {
-            g->tile_pack = dst;
-            g->n_tile_pack = (int32_t)n;
-        } else {
-            g->tile_wide = dst;
-            g->n_tile_wide = (int32_t)n;
-        }
-        if (n == 0) continue;
+    if (ntile > 0) {
         uint32_t *order = nullptr;
-        BBC_TRY(sc.get(&order, (size_t)n));
-        k_iota<<<grid_for(n), kThreads, 0, st>>>(order, n);
+        BBC_TRY(sc.get(&order, (size_t)ntile));
+        note_launch();
+        k_iota<<<grid_for(ntile), kThreads, 0, st>>>(order, ntile);
         BBC_LAUNCH_CHECK("k_iota");
-        BBC_TRY(radix_sort_pairs(keys, order, n, 16, st));
-        k_gather_items<<<grid_for(n), kThreads, 0, st>>>(src, order, n, dst);
+        BBC_TRY(radix_sort_pairs(keys, order, ntile, 16, st));
+        note_launch();
+        k_gather_items<<<grid_for(ntile), kThreads, 0, st>>>(raw, order, ntile, g->tile_items);
         BBC_LAUNCH_CHECK("k_gather_items");
     }
     g->items_tuning = t;
@@ -491,16 +479,19 @@ bbc_status prepare_graph(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_
     if (n_v > 0) BBC_CUDA_TRY(cudaMemsetAsync(deg_v, 0, (size_t)n_v * 4, st));
     BBC_CUDA_TRY(cudaMemsetAsync(stats, 0, 64, st));
     if (n_edges > 0) {
+        note_launch();
         k_validate_degrees<<<grid_for(n_edges), kThreads, 0, st>>>(
             du, dv, ds, n_edges, n_u, n_v, deg_u, deg_v, reinterpret_cast<unsigned *>(stats));
         BBC_LAUNCH_CHECK("k_validate_degrees");
     }
     // 2. per-side sum of C(d,2) and max degree
     if (n_u > 0) {
+        note_launch();
         k_degree_stats<<<grid_for(n_u), kThreads, 0, st>>>(deg_u, n_u, stats + 1);
         BBC_LAUNCH_CHECK("k_degree_stats");
     }
     if (n_v > 0) {
+        note_launch();
         k_degree_stats<<<grid_for(n_v), kThreads, 0, st>>>(deg_v, n_v, stats + 3);
         BBC_LAUNCH_CHECK("k_degree_stats");
     }
@@ -584,12 +575,15 @@ bbc_status prepare_graph(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_
     BBC_TRY(dev_alloc_n(&vB, (size_t)E, st));
     g->rowC = vB;
     if (E > 0) {
+        note_launch();
         k_map_edges<<<grid_for(E), kThreads, 0, st>>>(du, dv, ds, E, side, rankS, rankC, kA, vA);
         BBC_LAUNCH_CHECK("k_map_edges");
         BBC_TRY(radix_sort_pairs(kA, vA, E, bit_length((uint64_t)(nS > 0 ? nS - 1 : 0)), st));
+        note_launch();
         k_swap_sides<<<grid_for(E), kThreads, 0, st>>>(kA, vA, E, kB, vB);
         BBC_LAUNCH_CHECK("k_swap_sides");
         BBC_TRY(radix_sort_pairs(kB, vB, E, bit_length((uint64_t)(nC > 0 ? nC - 1 : 0)), st));
+        note_launch();
         k_count_duplicates<<<grid_for(E), kThreads, 0, st>>>(kB, vB, E, stats + 5);
         BBC_LAUNCH_CHECK("k_count_duplicates");
         unsigned long long dups = 0;
@@ -605,6 +599,7 @@ bbc_status prepare_graph(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_
             int64_t *pos = nullptr;
             BBC_TRY(sc.get(&flag, (size_t)E));
             BBC_TRY(sc.get(&pos, (size_t)E + 1));
+            note_launch();
             k_last_flags<<<grid_for(E), kThreads, 0, st>>>(kB, vB, E, flag);
             BBC_LAUNCH_CHECK("k_last_flags");
             BBC_TRY(exclusive_scan_i32_to_i64(flag, pos, E, st));
@@ -614,6 +609,7 @@ bbc_status prepare_graph(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_
             BBC_TRY(sc.get(&u2, (size_t)E2));
             BBC_TRY(sc.get(&v2, (size_t)E2));
             BBC_TRY(sc.get(&s2, (size_t)E2));
+            note_launch();
             k_dedup_last<<<grid_for(E), kThreads, 0, st>>>(kB, vB, E, pos, side, g->permS, g->permC,
                                                             u2, v2, s2);
             BBC_LAUNCH_CHECK("k_dedup_last");
@@ -629,11 +625,13 @@ bbc_status prepare_graph(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_
     BBC_TRY(dev_alloc_n(&g->rowS_off, (size_t)nS + 1, st));
     BBC_TRY(dev_alloc_n(&g->rowC_off, (size_t)nC + 1, st));
     if (nS > 0) {
+        note_launch();
         k_gather_deg<<<grid_for(nS), kThreads, 0, st>>>(degS, g->permS, nS, dr);
         BBC_LAUNCH_CHECK("k_gather_deg");
     }
     BBC_TRY(exclusive_scan_i32_to_i64(dr, g->rowS_off, nS, st));
     if (nC > 0) {
+        note_launch();
         k_gather_deg<<<grid_for(nC), kThreads, 0, st>>>(degC, g->permC, nC, dr);
         BBC_LAUNCH_CHECK("k_gather_deg");
     }
@@ -643,6 +641,7 @@ bbc_status prepare_graph(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_
     BBC_TRY(dev_alloc_n(&g->wl, (size_t)nS, st));
     if (nS > 0) BBC_CUDA_TRY(cudaMemsetAsync(g->wl, 0, (size_t)nS * 8, st));
     if (E > 0) {
+        note_launch();
         k_wedge_estimate<<<grid_for(E), kThreads, 0, st>>>(kA, g->rowS, E, g->rowC_off, g->rowC,
                                                              g->orient_low, g->wl);
         BBC_LAUNCH_CHECK("k_wedge_estimate");

@@ -179,6 +179,7 @@ bbc_status exclusive_scan(const Tin *in, Tout *out, int64_t n, cudaStream_t st) 
     }
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
     if (nb == 1) {
+        note_launch();
         k_scan_apply<Tin, Tout><<<1, kScanThreads, 0, st>>>(in, n, nullptr, out);
         BBC_CUDA_TRY(cudaGetLastError());
         return BBC_OK;
@@ -190,9 +191,11 @@ bbc_status exclusive_scan(const Tin *in, Tout *out, int64_t n, cudaStream_t st) 
         dev_free(sums, st);
         return s;
     }
+    note_launch();
     k_scan_block_sums<Tin, Tout><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums);
     s = exclusive_scan<Tout, Tout>(sums, pref, nb, st);
     if (s == BBC_OK) {
+        note_launch();
         k_scan_apply<Tin, Tout><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, pref, out);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = cuda_fail(e, "k_scan_apply");
@@ -229,9 +232,11 @@ bbc_status radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, int bits,
     for (int shift = 0; s == BBC_OK && shift < bits; shift += kRsBits) {
         const int width = bits - shift < kRsBits ? bits - shift : kRsBits;
         const uint32_t mask = (1u << width) - 1u;
+        note_launch();
         k_rs_histogram<<<(unsigned)ntiles, kRsThreads, 0, st>>>(ka, n, shift, mask, hist, (int)ntiles);
         s = exclusive_scan_u32(hist, offs, hn, st);
         if (s != BBC_OK) break;
+        note_launch();
         k_rs_scatter<<<(unsigned)ntiles, kRsThreads, 0, st>>>(ka, va, kb, vb, n, shift, mask, offs,
                                                                (int)ntiles);
         cudaError_t e = cudaGetLastError();

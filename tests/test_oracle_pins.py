@@ -276,3 +276,18 @@ def test_pins_pass_on_the_oracle():
 def test_each_planted_mistake_fails_a_pin(mutant):
     assert oracle._lib(mutant).bbco_mutant() == mutant
     assert _pin_failures(mutant), f"mutant {mutant} passed every pin"
+
+
+def test_anchor_samples_partition_the_count():
+    """Strided anchor samples with offsets 0..k-1 add up to the full count."""
+    g = synth.powerlaw_1m_200k(seed=6, scale=0.002)
+    full = oracle.count(g, per_vertex=False)
+    tot_b = tot_u = tot_w = 0
+    for off in range(3):
+        c, w = oracle.count_sample(g, stride=3, offset=off, threads=2, per_vertex=False)
+        tot_b += c.balanced
+        tot_u += c.unbalanced
+        tot_w += w
+    assert (tot_b, tot_u) == (full.balanced, full.unbalanced)
+    dv = np.bincount(g.v, minlength=g.n_v).astype(np.int64)
+    assert tot_w == int((dv * (dv - 1) // 2).sum())  # every oriented wedge exactly once
