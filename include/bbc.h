@@ -129,6 +129,30 @@ bbc_status bbc_count_async(bbc_graph *g, uint64_t *totals_dev, uint64_t *per_u,
                            uint64_t *per_v, const bbc_tuning *tuning, void *cuda_stream);
 
 /*
+ * bbc_count_noalloc -- bbc_count's global totals for a prepared graph, without any
+ * device or host allocation. The paper has no counterpart; this entry point exists for
+ * callers that cannot allocate at the time they count: code running while a stream is
+ * being captured into a CUDA graph (an allocation would be recorded into, or break,
+ * the capture), latency-critical loops that must not pay for an allocation's implicit
+ * synchronisation, and processes whose device memory is already reserved in full by
+ * another framework's allocator, where any new allocation fails.
+ *
+ *   g           a graph from bbc_prepare (its device layout is the input; unchanged).
+ *   totals_dev  device uint64[2], caller-owned: receives {balanced, unbalanced}.
+ *   cuda_stream the stream every launch is queued on; the call does not synchronise.
+ *
+ * The per-call scratch (queue head, kernel descriptor, one work item per pair-side
+ * vertex) lives in a 1 MiB static device array that every GPU loading this library
+ * holds until the process exits. Limit: graphs whose pair side has at most 65,520
+ * vertices; larger ones return BBC_E_INVALID_ARG with a message, before any launch.
+ * The first call on each device looks the array's address up (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture. All calls
+ * share the one array and each clears what must start at zero, so calls that overlap on
+ * the GPU (different streams, or threads without ordering) race and give wrong results.
+ */
+bbc_status bbc_count_noalloc(const bbc_graph *g, uint64_t *totals_dev, void *cuda_stream);
+
+/*
  * bbc_graph_info -- facts about a prepared graph (any output pointer may be NULL).
  *   side          0 when U is the pair side S, 1 when V is.
  *   wedges        W, the number of oriented wedges bbc_count visits

@@ -37,6 +37,7 @@ EXPORTS = (
     "bbc_graph_free", "bbc_count_batch", "bbc_autotune_batch", "bbc_server_create", "bbc_submit",
     "bbc_poll", "bbc_wait", "bbc_server_stats", "bbc_server_destroy", "bbc_status_string",
     "bbc_last_error", "bbc_launch_count", "bbc_profile_start", "bbc_profile_stop",
+    "bbc_count_noalloc",
 )
 
 
@@ -104,6 +105,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "bbc_profile_start": ([], ctypes.c_int),
             "bbc_profile_stop": ([ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)], ctypes.c_int),
             "bbc_last_error": ([], ctypes.c_char_p),
+            "bbc_count_noalloc": ([vp, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)

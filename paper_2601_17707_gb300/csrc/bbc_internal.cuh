@@ -150,6 +150,11 @@ struct CountLaunch {
 // Queues the counting kernels (dense tiles, then warp hash) on `st`.
 bbc_status launch_count(const CountLaunch &L, cudaStream_t st);
 
+// Launches only the tile kernel over `items` with `blocks` persistent blocks; touches no
+// memory but the arguments it is given.
+bbc_status launch_tile_only(const DevGraph *graphs, const TileItem *items, int n_items,
+                            unsigned *head, int tile_words, int blocks, cudaStream_t st);
+
 // Sets the kernels' shared-memory limits on the current device (idempotent); done
 // before any stream capture so that capture only records launches.
 bbc_status configure_count_kernels();

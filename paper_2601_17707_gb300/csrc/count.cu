@@ -625,6 +625,17 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
     return BBC_OK;
 }
 
+bbc_status launch_tile_only(const DevGraph *graphs, const TileItem *items, int n_items,
+                            unsigned *head, int tile_words, int blocks, cudaStream_t st) {
+    BBC_TRY(configure_count_kernels());
+    if (n_items <= 0) return BBC_OK;
+    note_launch();
+    k_tile<<<blocks, kTileThreads, (size_t)tile_words * 4, st>>>(graphs, items, n_items, head,
+                                                                 tile_words);
+    BBC_CUDA_TRY(cudaGetLastError());
+    return BBC_OK;
+}
+
 // An upper bound of the tile kernel's static shared memory (checked against the
 // compiled kernel when the kernels are configured).
 int tile_static_smem_bytes() { return (int)sizeof(ChunkSmem) + 512; }
