@@ -31,6 +31,10 @@ struct DevGraph {
     unsigned long long *bC;    // per-vertex balanced counts by C rank (nullable)
     unsigned long long *totals;// [0] balanced, [1] unbalanced
     const unsigned long long *wl; // oriented wedges per anchor rank (orders work items)
+    const uint2 *rng;          // per S -> C entry (a, c): the entries of row c that are
+                               // endpoints of a, as an index range [x, y) into rowC
+    uint32_t *cur;             // per S -> C entry: slice cursor carried across tiles
+                               // (nullable: slices are then found by binary search)
 };
 
 // A unit of work of the tile kernel: anchor `anchor` of graph `graph`, endpoint tiles

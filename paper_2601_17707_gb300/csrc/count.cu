@@ -214,7 +214,6 @@ template <int CW>
 struct TileCounter {
     uint32_t *tile;
     uint32_t lo;
-    static constexpr int kPerWord2 = CW == 0 ? 4 : (CW == 1 ? 2 : 1);  // endpoints per 2 words
     __device__ __forceinline__ void bump(uint32_t w, uint32_t t) const {
         const uint32_t e = w - lo;
         if (CW == 0)
@@ -299,51 +298,114 @@ __device__ __forceinline__ void wedge(const TileCounter<CW> &ctr, uint32_t x, ui
         acc += ctr.peek(x & kIdMask, t) - 1u;
 }
 
+// First index of row[b, lim) whose rank is >= key (the row is sorted by rank), found by
+// galloping from b: about 2 log2 of the distance instead of log2 of the row length.
+__device__ __forceinline__ uint32_t gallop_rank(const uint32_t *__restrict__ row, uint32_t b,
+                                                uint32_t lim, uint32_t key) {
+    uint32_t lo = b, step = 1;
+    while (lo + step <= lim && (__ldg(row + lo + step - 1) & kIdMask) < key) {
+        lo += step;
+        step <<= 1;
+    }
+    uint32_t hi = min(lo + step - 1, lim);
+    while (lo < hi) {
+        const uint32_t m = (lo + hi) >> 1;
+        if ((__ldg(row + m) & kIdMask) < key)
+            lo = m + 1;
+        else
+            hi = m;
+    }
+    return lo;
+}
+
+// Where one tile's slices come from.
+struct SweepCtx {
+    uint32_t lo, hi;              // the tile's endpoint ranks [lo, hi)
+    uint32_t range_lo, range_hi;  // the anchor's whole endpoint range
+    bool carry;                   // a previous tile of this item ended where this one starts
+    bool single;                  // all centres fit one chunk: slices stay in shared memory
+    bool use_cur;                 // multi-chunk anchor owned by this block: cursors in G.cur
+    bool last_pass;               // the last sweep over this tile (cursors advance after it)
+};
+
+// The slice of row c (entry e of the anchor's S -> C row) whose endpoint ranks lie in
+// [X.lo, X.hi). The anchor's whole range inside row c is known from preparation (rng), so
+// the first and last tiles need no search; other starts are carried from the previous
+// tile and other ends found by galloping.
+__device__ __forceinline__ void find_slice(const DevGraph &G, int64_t e, const SweepCtx &X,
+                                           uint32_t prev_end, bool have_prev, uint32_t &start,
+                                           uint32_t &len) {
+    const uint2 r = __ldg(G.rng + e);
+    const uint32_t rlo = r.x, rhi = r.y;
+    uint32_t b;
+    if (X.lo == X.range_lo)
+        b = rlo;
+    else if (have_prev)
+        b = prev_end;
+    else
+        b = (uint32_t)lower_bound_rank(G.rowC, rlo, rhi, X.lo);
+    const uint32_t en = X.hi >= X.range_hi ? rhi : gallop_rank(G.rowC, b, min(rhi, b + (X.hi - X.lo)), X.hi);
+    start = b;
+    len = en - b;
+}
+
 // One pass of the whole block over the oriented wedges of anchor rows [sb, se) whose
-// endpoints lie in [lo, hi), in chunks of kChunk centres. Per chunk, every thread finds
-// its centre's slice (binary search in the rank-sorted C -> S row); slices shorter than
-// kLongMin are concatenated and cut into equal contiguous shares, one per thread; longer
-// ones are cut into kPiece-wedge pieces that warps pull from a shared counter and sweep
-// with coalesced 16-byte loads. MODE 0 bumps the counters; MODE 1 reads them and adds
-// (count - 1) per wedge to the centre's per-vertex sum.
+// endpoints lie in [X.lo, X.hi), in chunks of kChunk centres. Per chunk, every thread
+// finds its centre's slice; slices shorter than kLongMin are concatenated and cut into
+// equal contiguous shares, one per thread; longer ones are cut into kPiece-wedge pieces
+// that warps pull from a shared counter and sweep with coalesced 16-byte loads. MODE 0
+// bumps the counters; MODE 1 reads them and adds (count - 1) per wedge to the centre's
+// per-vertex sum. A single-chunk MODE 1 pass reuses the slices MODE 0 just found.
 template <int MODE, int CW>
-__device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, uint32_t lo, uint32_t hi,
+__device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const SweepCtx &X,
                             const TileCounter<CW> &ctr, ChunkSmem &cs) {
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t *__restrict__ rowC = G.rowC;
     for (int64_t cb = sb; cb < se; cb += kChunk) {
         const int64_t ci = cb + tid;
-        uint32_t start = 0, len = 0, ent = 0;
-        if (ci < se) {
-            ent = __ldg(G.rowS + ci);
-            const uint32_t c = ent & kIdMask;
-            const int64_t rb = __ldg(G.rowC_off + c), re = __ldg(G.rowC_off + c + 1);
-            const int64_t b = lo == 0 ? rb : lower_bound_rank(rowC, rb, re, lo);
-            const int64_t e = hi >= (uint32_t)G.nS ? re : lower_bound_rank(rowC, b, re, hi);
-            start = (uint32_t)b;
-            len = (uint32_t)(e - b);
+        uint32_t ent = 0;
+        if (MODE == 1 && X.single) {
+            ent = cs.ent[tid];
+            cs.acc[tid] = 0;
+            if (tid == 0) cs.piece_ctr = 0;
+            __syncthreads();
+        } else {
+            uint32_t start = 0, len = 0;
+            if (ci < se) {
+                ent = __ldg(G.rowS + ci);
+                uint32_t prev = 0;
+                bool have_prev = false;
+                if (X.carry && X.single) {
+                    prev = cs.start[tid] + cs.len[tid];
+                    have_prev = true;
+                } else if (X.carry && X.use_cur) {
+                    prev = G.cur[ci];
+                    have_prev = true;
+                }
+                find_slice(G, ci, X, prev, have_prev, start, len);
+                if (X.use_cur && X.last_pass) G.cur[ci] = start + len;
+            }
+            const bool islong = len >= (uint32_t)kLongMin;
+            const unsigned long long mine =
+                ((unsigned long long)(islong ? (len + kPiece - 1) / kPiece : 0u) << 32) |
+                (islong ? 0u : len);
+            __shared__ unsigned long long s_total;
+            const unsigned long long ex = block_exclusive_scan_u64(mine, &s_total, cs.wsum);
+            cs.start[tid] = start;
+            cs.len[tid] = len;
+            cs.ent[tid] = ent;
+            cs.pshort[tid] = (uint32_t)ex;
+            cs.ppiece[tid] = (uint32_t)(ex >> 32);
+            if (MODE == 1) cs.acc[tid] = 0;
+            if (tid == 0) cs.piece_ctr = 0;
+            const unsigned long long total = s_total;
+            if (tid == kChunk - 1) {
+                cs.pshort[kChunk] = (uint32_t)total;
+                cs.ppiece[kChunk] = (uint32_t)(total >> 32);
+            }
+            __syncthreads();
         }
-        const bool islong = len >= (uint32_t)kLongMin;
-        const unsigned long long mine =
-            ((unsigned long long)(islong ? (len + kPiece - 1) / kPiece : 0u) << 32) |
-            (islong ? 0u : len);
-        unsigned long long total;
-        __shared__ unsigned long long s_total;
-        const unsigned long long ex = block_exclusive_scan_u64(mine, &s_total, cs.wsum);
-        cs.start[tid] = start;
-        cs.len[tid] = len;
-        cs.ent[tid] = ent;
-        cs.pshort[tid] = (uint32_t)ex;
-        cs.ppiece[tid] = (uint32_t)(ex >> 32);
-        if (MODE == 1) cs.acc[tid] = 0;
-        if (tid == 0) cs.piece_ctr = 0;
-        total = s_total;
-        if (tid == kChunk - 1) {
-            cs.pshort[kChunk] = (uint32_t)total;
-            cs.ppiece[kChunk] = (uint32_t)(total >> 32);
-        }
-        __syncthreads();
-        const uint32_t NS = (uint32_t)total, NP = (uint32_t)(total >> 32);
+        const uint32_t NS = cs.pshort[kChunk], NP = cs.ppiece[kChunk];
         // short slices: contiguous equal shares
         if (NS) {
             uint32_t k = (uint32_t)(((unsigned long long)NS * tid) / kChunk);
@@ -419,7 +481,10 @@ __device__ __forceinline__ void pair_total(unsigned long long p, unsigned long l
 }
 
 // Reads, reduces and clears the tile of endpoints [lo, hi). Words past the last
-// endpoint in the final 16-byte group are never bumped and stay zero.
+// endpoint in the final 16-byte group are never bumped and stay zero. With 8-bit
+// counters a word holds the bytes (p0, n0, p1, n1) of two endpoints, and
+// sum C(x, 2) = (sum x^2 - sum x) / 2 over its bytes, while p0 n0 + p1 n1 is half the
+// byte dot product of the word with its pair-swapped self: three dp4a per word.
 template <int CW>
 __device__ __forceinline__ void tile_epilogue(uint32_t *tile, uint32_t lo, uint32_t hi,
                                               unsigned long long *bS, unsigned long long &bal,
@@ -431,23 +496,43 @@ __device__ __forceinline__ void tile_epilogue(uint32_t *tile, uint32_t lo, uint3
     for (uint32_t i = threadIdx.x; i < n4; i += blockDim.x) {
         const uint4 q = t4[i];
         if ((q.x | q.y | q.z | q.w) == 0) continue;
+        t4[i] = make_uint4(0, 0, 0, 0);
         if (CW == 0) {
             const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+            uint32_t sq = 0, s1 = 0, pn2 = 0;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const uint32_t e = lo + 8 * i + 2 * k;
-                pair_total(w4[k] & 0xffu, (w4[k] >> 8) & 0xffu, bS, e, bal, unb);
-                pair_total((w4[k] >> 16) & 0xffu, w4[k] >> 24, bS, e + 1, bal, unb);
+                sq = __dp4a(w4[k], w4[k], sq);
+                s1 = __dp4a(w4[k], 0x01010101u, s1);
+                pn2 = __dp4a(w4[k], __byte_perm(w4[k], 0u, 0x2301), pn2);
+            }
+            bal += (sq - s1) >> 1;
+            unb += pn2 >> 1;
+            if (bS) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t lo16 = w4[k] & 0xffffu, hi16 = w4[k] >> 16;
+                    const uint32_t f0 = (__dp4a(lo16, lo16, 0u) - __dp4a(lo16, 0x0101u, 0u)) >> 1;
+                    const uint32_t f1 = (__dp4a(hi16, hi16, 0u) - __dp4a(hi16, 0x0101u, 0u)) >> 1;
+                    if (f0) atomicAdd(bS + lo + 8 * i + 2 * k, (unsigned long long)f0);
+                    if (f1) atomicAdd(bS + lo + 8 * i + 2 * k + 1, (unsigned long long)f1);
+                }
             }
         } else if (CW == 1) {
             const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-            for (int k = 0; k < 4; ++k) pair_total(w4[k] & 0xffffu, w4[k] >> 16, bS, lo + 4 * i + k, bal, unb);
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t p = w4[k] & 0xffffu, m = w4[k] >> 16;
+                // each product is even and below 2^32, so the halves add without overflow
+                const uint32_t f = ((p * (p - (p > 0))) >> 1) + ((m * (m - (m > 0))) >> 1);
+                bal += f;
+                unb += p * m;
+                if (bS && f) atomicAdd(bS + lo + 4 * i + k, (unsigned long long)f);
+            }
         } else {
             pair_total(q.x, q.y, bS, lo + 2 * i, bal, unb);
             pair_total(q.z, q.w, bS, lo + 2 * i + 1, bal, unb);
         }
-        t4[i] = make_uint4(0, 0, 0, 0);
     }
 }
 
@@ -457,16 +542,25 @@ __device__ void run_tile_item(const DevGraph &G, const TileItem &item, int tile_
     const int a = item.anchor;
     const int64_t sb = G.rowS_off[a], se = G.rowS_off[a + 1];
     const uint32_t ept = endpoints_per_tile(CW, (uint32_t)tile_words);
-    const uint32_t range_lo = G.orient_low ? 0u : (uint32_t)a + 1u;
-    const uint32_t range_hi = G.orient_low ? (uint32_t)a : (uint32_t)G.nS;
-    const int t1 = tile_end_of(item);
-    for (int t = item.tile_begin; t < t1; ++t) {
-        const uint32_t lo = range_lo + (uint32_t)t * ept;
-        const uint32_t hi = min(lo + ept, range_hi);
-        const TileCounter<CW> ctr{tile, lo};
-        block_sweep<0>(G, sb, se, lo, hi, ctr, cs);
-        if (G.bC) block_sweep<1>(G, sb, se, lo, hi, ctr, cs);
-        tile_epilogue<CW>(tile, lo, hi, G.bS, bal, unb);
+    SweepCtx X;
+    X.range_lo = G.orient_low ? 0u : (uint32_t)a + 1u;
+    X.range_hi = G.orient_low ? (uint32_t)a : (uint32_t)G.nS;
+    const int t0 = item.tile_begin, t1 = tile_end_of(item);
+    const int nt_all = (int)((X.range_hi - X.range_lo + ept - 1) / ept);
+    X.single = se - sb <= kChunk;
+    X.use_cur = !X.single && G.cur != nullptr && t0 == 0 && t1 == nt_all;
+    for (int t = t0; t < t1; ++t) {
+        X.lo = X.range_lo + (uint32_t)t * ept;
+        X.hi = min(X.lo + ept, X.range_hi);
+        X.carry = t > t0;
+        const TileCounter<CW> ctr{tile, X.lo};
+        X.last_pass = G.bC == nullptr;
+        block_sweep<0>(G, sb, se, X, ctr, cs);
+        if (G.bC) {
+            X.last_pass = true;
+            block_sweep<1>(G, sb, se, X, ctr, cs);
+        }
+        tile_epilogue<CW>(tile, X.lo, X.hi, G.bS, bal, unb);
         __syncthreads();
     }
 }

@@ -23,6 +23,8 @@ struct bbc_graph {
     int32_t *permS = nullptr;  // rank -> original id
     int32_t *permC = nullptr;
     unsigned long long *wl = nullptr;  // oriented wedges per anchor rank
+    uint2 *rng = nullptr;      // per S -> C entry (a, c): a's endpoint range [x, y) in rowC
+    uint32_t *cur = nullptr;   // per S -> C entry: slice cursor of the tile kernel (scratch)
 
     // work lists (rebuilt when the tuning changes)
     bbc::Tuning items_tuning{};

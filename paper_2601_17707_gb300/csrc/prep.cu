@@ -190,11 +190,13 @@ __device__ __forceinline__ int64_t lower_bound_rank(const uint32_t *__restrict__
 
 // wl[a] = number of oriented wedges at anchor a: for every entry (a, c) of the S -> C
 // rows, the entries of row c of higher (orient_low: lower) rank than a. The rows are
-// grouped by anchor, so a segmented warp sum leaves one atomic per anchor run.
+// grouped by anchor, so a segmented warp sum leaves one atomic per anchor run. The
+// anchor's endpoint range inside row c (the entries after a, or before a with orient_low)
+// is kept as rng[e], so the counting kernels find every slice without a row-offset load.
 __global__ void k_wedge_estimate(const uint32_t *__restrict__ anchor_of, const uint32_t *__restrict__ rowS,
                                  int64_t n, const int64_t *__restrict__ rowC_off,
                                  const uint32_t *__restrict__ rowC, int orient_low,
-                                 unsigned long long *__restrict__ wl) {
+                                 unsigned long long *__restrict__ wl, uint2 *__restrict__ rng) {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
@@ -207,6 +209,8 @@ __global__ void k_wedge_estimate(const uint32_t *__restrict__ anchor_of, const u
             const uint32_t c = rowS[e] & kIdMask;
             const int64_t b = rowC_off[c], en = rowC_off[c + 1];
             const int64_t p = lower_bound_rank(rowC, b, en, a);
+            rng[e] = orient_low ? make_uint2((uint32_t)b, (uint32_t)p)
+                                : make_uint2((uint32_t)p + 1u, (uint32_t)en);
             cnt = orient_low ? (unsigned long long)(p - b) : (unsigned long long)(en - p - 1);
         }
 #pragma unroll
@@ -369,12 +373,14 @@ DevGraph host_descriptor(const bbc_graph *g, bool per_vertex) {
     d.bC = per_vertex ? g->bC : nullptr;
     d.totals = g->totals;
     d.wl = g->wl;
+    d.rng = g->rng;
+    d.cur = g->cur;
     return d;
 }
 
 void release_graph(bbc_graph *g, cudaStream_t st) {
     if (!g) return;
-    void *ptrs[] = {g->rowS_off, g->rowS, g->rowC_off, g->rowC, g->permS, g->permC, g->wl,
+    void *ptrs[] = {g->rowS_off, g->rowS, g->rowC_off, g->rowC, g->permS, g->permC, g->wl, g->rng, g->cur,
                     g->tile_items, g->warp_items, g->dgraph, g->bS, g->bC,
                     g->totals, g->queue};
     for (void *p : ptrs)
@@ -383,6 +389,10 @@ void release_graph(bbc_graph *g, cudaStream_t st) {
 }
 
 bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
+    if (!g->cur && g->n_edges > 0) {
+        BBC_TRY(dev_alloc_n(&g->cur, (size_t)g->n_edges, st));
+        g->device_bytes += (size_t)g->n_edges * 4;
+    }
     if (g->items_valid && g->items_tuning.tile_words == t.tile_words &&
         g->items_tuning.warp_max_wedges == t.warp_max_wedges &&
         g->items_tuning.split_wedges == t.split_wedges)
@@ -639,17 +649,18 @@ bbc_status prepare_graph(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_
 
     // 6. oriented wedges per anchor
     BBC_TRY(dev_alloc_n(&g->wl, (size_t)nS, st));
+    BBC_TRY(dev_alloc_n(&g->rng, (size_t)E, st));
     if (nS > 0) BBC_CUDA_TRY(cudaMemsetAsync(g->wl, 0, (size_t)nS * 8, st));
     if (E > 0) {
         note_launch();
         k_wedge_estimate<<<grid_for(E), kThreads, 0, st>>>(kA, g->rowS, E, g->rowC_off, g->rowC,
-                                                             g->orient_low, g->wl);
+                                                             g->orient_low, g->wl, g->rng);
         BBC_LAUNCH_CHECK("k_wedge_estimate");
     }
     BBC_TRY(dev_alloc_n(&g->totals, 2, st));
     BBC_TRY(dev_alloc_n(&g->queue, 1, st));
     BBC_TRY(dev_alloc_n(&g->dgraph, 1, st));
-    g->device_bytes = (size_t)(nS + 1 + nC + 1) * 8 + (size_t)E * 8 + (size_t)(nS + nC) * 4 +
+    g->device_bytes = (size_t)(nS + 1 + nC + 1) * 8 + (size_t)E * 16 + (size_t)(nS + nC) * 4 +
                       (size_t)nS * 8;
     *out = g;
     guard.g = nullptr;
