@@ -22,13 +22,6 @@ namespace {
 
 constexpr int kThreads = 256;
 
-struct CopyJob {
-    const void *src;
-    int64_t dst;
-    int32_t n;
-    int32_t graph;
-};
-
 template <class Item>
 __global__ void k_concat_items(const CopyJob *__restrict__ jobs, Item *__restrict__ dst) {
     const CopyJob j = jobs[blockIdx.x];
@@ -337,6 +330,20 @@ Tuning batch_tuning(int32_t n, bbc_graph *const *gs, const bbc_tuning *t) {
 }
 
 }  // namespace
+
+bbc_status concat_items(const std::vector<CopyJob> &jobs, bool tiles, void *dst, CopyJob *djobs,
+                        cudaStream_t st) {
+    if (jobs.empty()) return BBC_OK;
+    BBC_CUDA_TRY(cudaMemcpyAsync(djobs, jobs.data(), sizeof(CopyJob) * jobs.size(),
+                                 cudaMemcpyHostToDevice, st));
+    note_launch();
+    if (tiles)
+        k_concat_items<TileItem><<<(unsigned)jobs.size(), kThreads, 0, st>>>(djobs, static_cast<TileItem *>(dst));
+    else
+        k_concat_items<HashItem><<<(unsigned)jobs.size(), kThreads, 0, st>>>(djobs, static_cast<HashItem *>(dst));
+    BBC_CUDA_TRY(cudaGetLastError());
+    return BBC_OK;
+}
 
 bbc_status count_batch_impl(int32_t n, bbc_graph *const *gs, uint64_t *balanced,
                             const bbc_tuning *tuning, cudaStream_t st, float *ms) {

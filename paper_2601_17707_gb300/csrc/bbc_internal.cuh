@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/bbc.h"
 
@@ -150,6 +151,21 @@ struct CountLaunch {
     QueueState *queue;          // device, zeroed by the caller before the launch
     Tuning tuning;
 };
+
+// One contiguous run of a graph's work items to copy into a combined list, tagged with
+// the graph's index in that list's descriptor array.
+struct CopyJob {
+    const void *src;
+    int64_t dst;
+    int32_t n;
+    int32_t graph;
+};
+
+// Copies every job's items (TileItem when `tiles`, else HashItem) into `dst` with one
+// kernel; `djobs` is device scratch for jobs.size() entries (the copy of `jobs` into it
+// is a pageable host-to-device copy, so `jobs` may be released on return).
+bbc_status concat_items(const std::vector<CopyJob> &jobs, bool tiles, void *dst, CopyJob *djobs,
+                        cudaStream_t st);
 
 // Queues the counting kernels (dense tiles, then warp hash) on `st`.
 bbc_status launch_count(const CountLaunch &L, cudaStream_t st);

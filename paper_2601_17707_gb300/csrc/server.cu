@@ -1,0 +1,403 @@
+// server.cu -- the serving loop of include/bbc.h (bbc_server_*, bbc_submit, bbc_poll,
+// bbc_wait): continuous batching of many graph-counting requests on one GPU.
+//
+// Requests are copied at submit time and queued. A worker thread runs ticks:
+//   1. admission: queued requests are admitted in arrival order while the device memory
+//      reserved for admitted requests plus theirs stays within the budget;
+//   2. newly admitted requests are prepared (bbc_prepare's pipeline) on the server's
+//      stream and their counts zeroed; their device layout stays resident until done;
+//   3. one launch of the counting kernels covers every admitted graph: all remaining work
+//      items of the small ones and a bounded chunk of each large one, so a large request
+//      advances over several ticks (its partial totals stay in device memory between
+//      ticks) and never holds small requests back for long;
+//   4. requests whose work items are all counted complete: their totals are read back,
+//      their device memory is freed and the reservation released.
+// Requests that arrive while a tick runs join at the next tick: the GPU work of all
+// admitted requests overlaps inside each tick's launch.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "graph.cuh"
+
+namespace bbc {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t ticket = 0;
+    int32_t n_u = 0, n_v = 0;
+    int64_t n_edges = 0;
+    std::vector<int32_t> u, v;
+    std::vector<int8_t> s;
+    size_t reserve = 0;          // device bytes reserved at admission
+    bbc_graph *g = nullptr;
+    int32_t tile_done = 0, warp_done = 0;
+    bool done = false;
+    bbc_status status = BBC_OK;
+    uint64_t balanced = 0;
+    Clock::time_point t_submit, t_done;
+};
+
+// Device memory a request may hold at its peak (preparation temporaries included).
+size_t reservation_bytes(int32_t n_u, int32_t n_v, int64_t n_edges) {
+    return (size_t)n_edges * 56 + ((size_t)n_u + (size_t)n_v) * 48 + (size_t(1) << 20);
+}
+
+template <class T>
+bbc_status ensure(T **buf, size_t *cap, size_t need, cudaStream_t st) {
+    if (*cap >= need && *buf) return BBC_OK;
+    if (*buf) dev_free(*buf, st);
+    *buf = nullptr;
+    size_t n = std::max(need, *cap * 2);
+    BBC_TRY(dev_alloc_n(buf, n, st));
+    *cap = n;
+    return BBC_OK;
+}
+
+}  // namespace
+}  // namespace bbc
+
+struct bbc_server {
+    size_t budget = 0;
+    bbc::Tuning tuning{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<bbc::Request *> queue;
+    std::vector<bbc::Request *> active;
+    std::unordered_map<uint64_t, bbc::Request *> all;
+    size_t reserved = 0;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::thread worker;
+    std::vector<double> latencies_us;
+    // tick buffers (grown as needed)
+    bbc::DevGraph *dgraphs = nullptr;
+    size_t dgraphs_cap = 0;
+    bbc::TileItem *tiles = nullptr;
+    size_t tiles_cap = 0;
+    bbc::HashItem *warps = nullptr;
+    size_t warps_cap = 0;
+    bbc::CopyJob *djobs = nullptr;
+    size_t djobs_cap = 0;
+    bbc::QueueState *queue_state = nullptr;
+    unsigned long long *host_totals = nullptr;  // pinned, 2 per active request
+    size_t host_totals_cap = 0;
+};
+
+namespace bbc {
+namespace {
+
+void finish_locked(bbc_server *S, Request *r, bbc_status st, uint64_t balanced) {
+    r->status = st;
+    r->balanced = balanced;
+    r->done = true;
+    r->t_done = Clock::now();
+    r->u = {};
+    r->v = {};
+    r->s = {};
+    if (st == BBC_OK)
+        S->latencies_us.push_back(
+            std::chrono::duration<double, std::micro>(r->t_done - r->t_submit).count());
+}
+
+// Prepares one admitted request; on failure the request completes with that status.
+bool admit_one(bbc_server *S, Request *r) {
+    bbc_graph *g = nullptr;
+    bbc_status st = prepare_graph(r->n_u, r->n_v, r->n_edges, r->u.data(), r->v.data(),
+                                  r->s.data(), 0u, S->stream, &g);
+    if (st == BBC_OK) st = build_work_lists(g, S->tuning, S->stream);
+    if (st == BBC_OK) {
+        cudaError_t e = cudaMemsetAsync(g->totals, 0, 16, S->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "server totals");
+    }
+    if (st != BBC_OK) {
+        if (g) release_graph(g, S->stream);
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->reserved -= r->reserve;
+        finish_locked(S, r, st, 0);
+        S->cv_done.notify_all();
+        return false;
+    }
+    r->g = g;
+    r->u = {};
+    r->v = {};
+    r->s = {};
+    return true;
+}
+
+// One tick over the active requests: a combined work list and one counting launch.
+bbc_status run_tick(bbc_server *S, std::vector<Request *> &act) {
+    cudaStream_t st = S->stream;
+    const int chunk = 4 * device_sm_count() * S->tuning.blocks_per_sm;
+    const size_t n = act.size();
+    std::vector<DevGraph> hd(n);
+    std::vector<CopyJob> jt, jh;
+    int64_t nt = 0, nh = 0;
+    std::vector<int32_t> take_t(n), take_h(n);
+    for (size_t i = 0; i < n; ++i) {
+        bbc_graph *g = act[i]->g;
+        hd[i] = host_descriptor(g, false);
+        const int32_t rt = g->n_tile - act[i]->tile_done;
+        const int32_t rh = g->n_warp - act[i]->warp_done;
+        take_t[i] = std::min(rt, chunk);
+        take_h[i] = std::min(rh, 64 * chunk);
+        if (take_t[i] > 0)
+            jt.push_back(CopyJob{g->tile_items + act[i]->tile_done, nt, take_t[i], (int32_t)i});
+        if (take_h[i] > 0)
+            jh.push_back(CopyJob{g->warp_items + act[i]->warp_done, nh, take_h[i], (int32_t)i});
+        nt += take_t[i];
+        nh += take_h[i];
+    }
+    BBC_TRY(ensure(&S->dgraphs, &S->dgraphs_cap, n, st));
+    BBC_TRY(ensure(&S->tiles, &S->tiles_cap, (size_t)std::max<int64_t>(nt, 1), st));
+    BBC_TRY(ensure(&S->warps, &S->warps_cap, (size_t)std::max<int64_t>(nh, 1), st));
+    BBC_TRY(ensure(&S->djobs, &S->djobs_cap, std::max(jt.size(), jh.size()) + 1, st));
+    if (!S->queue_state) BBC_TRY(dev_alloc_n(&S->queue_state, 1, st));
+    if (S->host_totals_cap < 2 * n) {
+        if (S->host_totals) cudaFreeHost(S->host_totals);
+        S->host_totals = nullptr;
+        S->host_totals_cap = std::max<size_t>(2 * n, 2 * S->host_totals_cap);
+        BBC_CUDA_TRY(cudaMallocHost(&S->host_totals, sizeof(unsigned long long) * S->host_totals_cap));
+    }
+    BBC_CUDA_TRY(cudaMemcpyAsync(S->dgraphs, hd.data(), sizeof(DevGraph) * n, cudaMemcpyHostToDevice, st));
+    BBC_TRY(concat_items(jt, true, S->tiles, S->djobs, st));
+    BBC_TRY(concat_items(jh, false, S->warps, S->djobs, st));
+    BBC_CUDA_TRY(cudaMemsetAsync(S->queue_state, 0, sizeof(QueueState), st));
+    CountLaunch L{};
+    L.graphs = S->dgraphs;
+    L.tile_items = S->tiles;
+    L.n_tile_items = (int32_t)nt;
+    L.warp_items = S->warps;
+    L.n_warp_items = (int32_t)nh;
+    L.queue = S->queue_state;
+    L.tuning = S->tuning;
+    BBC_TRY(launch_count(L, st));
+    for (size_t i = 0; i < n; ++i) {
+        act[i]->tile_done += take_t[i];
+        act[i]->warp_done += take_h[i];
+        BBC_CUDA_TRY(cudaMemcpyAsync(S->host_totals + 2 * i, act[i]->g->totals, 16,
+                                     cudaMemcpyDeviceToHost, st));
+    }
+    QueueState qs{};
+    BBC_CUDA_TRY(cudaMemcpyAsync(&qs, S->queue_state, sizeof qs, cudaMemcpyDeviceToHost, st));
+    BBC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (qs.error) {
+        set_error("serving tick: counting kernel reported an internal inconsistency");
+        return BBC_E_CUDA;
+    }
+    return BBC_OK;
+}
+
+void worker_main(bbc_server *S) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        std::vector<Request *> admitted;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty() || !S->active.empty(); });
+            if (S->stop) break;
+            while (!S->queue.empty() && S->reserved + S->queue.front()->reserve <= S->budget) {
+                Request *r = S->queue.front();
+                S->queue.pop_front();
+                S->reserved += r->reserve;
+                admitted.push_back(r);
+            }
+        }
+        std::vector<Request *> fresh;
+        for (Request *r : admitted)
+            if (admit_one(S, r)) fresh.push_back(r);
+        std::vector<Request *> act;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            for (Request *r : fresh) S->active.push_back(r);
+            act = S->active;
+        }
+        if (act.empty()) continue;
+        const bbc_status st = run_tick(S, act);
+        std::lock_guard<std::mutex> lk(S->mu);
+        std::vector<Request *> still;
+        for (size_t i = 0; i < act.size(); ++i) {
+            Request *r = act[i];
+            const bool complete = r->tile_done >= r->g->n_tile && r->warp_done >= r->g->n_warp;
+            if (st != BBC_OK || complete) {
+                release_graph(r->g, S->stream);
+                r->g = nullptr;
+                S->reserved -= r->reserve;
+                finish_locked(S, r, st, st == BBC_OK ? S->host_totals[2 * i] : 0);
+            } else {
+                still.push_back(r);
+            }
+        }
+        S->active = still;
+        S->cv_done.notify_all();
+    }
+}
+
+}  // namespace
+}  // namespace bbc
+
+using namespace bbc;
+
+extern "C" {
+
+bbc_status bbc_server_create(size_t device_budget_bytes, const bbc_tuning *tuning, bbc_server **out) {
+    if (!out || device_budget_bytes == 0) {
+        set_error("bbc_server_create: NULL output or zero budget");
+        return BBC_E_INVALID_ARG;
+    }
+    try {
+        bbc_server *S = new bbc_server();
+        S->budget = device_budget_bytes;
+        S->tuning = resolve_tuning(tuning, device_sm_count());
+        if (S->tuning.split_wedges == 0) S->tuning.split_wedges = (long long)1 << 26;
+        cudaGetDevice(&S->device);
+        cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete S;
+            return cuda_fail(e, "bbc_server_create stream");
+        }
+        S->worker = std::thread(worker_main, S);
+        *out = S;
+        return BBC_OK;
+    } catch (...) {
+        set_error("bbc_server_create failed");
+        return BBC_E_NO_MEMORY;
+    }
+}
+
+bbc_status bbc_submit(bbc_server *S, int32_t n_u, int32_t n_v, int64_t n_edges, const int32_t *u,
+                      const int32_t *v, const int8_t *sign, uint64_t *ticket) {
+    if (!S || !ticket || n_u < 0 || n_v < 0 || n_edges < 0 || (n_edges > 0 && (!u || !v || !sign))) {
+        set_error("bbc_submit: bad arguments");
+        return BBC_E_INVALID_ARG;
+    }
+    const size_t need = reservation_bytes(n_u, n_v, n_edges);
+    if (need > S->budget) {
+        set_error("bbc_submit: the request alone needs more device memory than the budget");
+        return BBC_E_OVER_BUDGET;
+    }
+    try {
+        Request *r = new Request();
+        r->n_u = n_u;
+        r->n_v = n_v;
+        r->n_edges = n_edges;
+        r->u.assign(u, u + n_edges);
+        r->v.assign(v, v + n_edges);
+        r->s.assign(sign, sign + n_edges);
+        r->reserve = need;
+        r->t_submit = Clock::now();
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop) {
+            delete r;
+            return BBC_E_CANCELLED;
+        }
+        r->ticket = S->next_ticket++;
+        S->all[r->ticket] = r;
+        S->queue.push_back(r);
+        *ticket = r->ticket;
+        S->cv_work.notify_one();
+        return BBC_OK;
+    } catch (...) {
+        set_error("bbc_submit: host allocation failed");
+        return BBC_E_NO_MEMORY;
+    }
+}
+
+bbc_status bbc_poll(bbc_server *S, uint64_t ticket, uint64_t *balanced) {
+    if (!S) return BBC_E_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end()) {
+        set_error("bbc_poll: unknown ticket");
+        return BBC_E_INVALID_ARG;
+    }
+    Request *r = it->second;
+    if (!r->done) return BBC_E_NOT_READY;
+    if (balanced && r->status == BBC_OK) *balanced = r->balanced;
+    return r->status;
+}
+
+bbc_status bbc_wait(bbc_server *S, uint64_t ticket, int64_t timeout_us, uint64_t *balanced) {
+    if (!S) return BBC_E_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end()) {
+        set_error("bbc_wait: unknown ticket");
+        return BBC_E_INVALID_ARG;
+    }
+    Request *r = it->second;
+    auto ready = [&] { return r->done; };
+    if (timeout_us < 0)
+        S->cv_done.wait(lk, ready);
+    else if (!S->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready))
+        return BBC_E_TIMEOUT;
+    if (balanced && r->status == BBC_OK) *balanced = r->balanced;
+    return r->status;
+}
+
+bbc_status bbc_server_stats(bbc_server *S, uint64_t *completed, double *p50_us, double *p99_us,
+                            double *mean_us) {
+    if (!S) return BBC_E_INVALID_ARG;
+    std::vector<double> lat;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        lat = S->latencies_us;
+    }
+    if (completed) *completed = lat.size();
+    double p50 = 0, p99 = 0, mean = 0;
+    if (!lat.empty()) {
+        std::sort(lat.begin(), lat.end());
+        auto pct = [&](double q) {
+            const size_t k = std::min(lat.size() - 1, (size_t)(q * (double)(lat.size() - 1) + 0.5));
+            return lat[k];
+        };
+        p50 = pct(0.50);
+        p99 = pct(0.99);
+        for (double x : lat) mean += x;
+        mean /= (double)lat.size();
+    }
+    if (p50_us) *p50_us = p50;
+    if (p99_us) *p99_us = p99;
+    if (mean_us) *mean_us = mean;
+    return BBC_OK;
+}
+
+void bbc_server_destroy(bbc_server *S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        for (Request *r : S->queue) finish_locked(S, r, BBC_E_CANCELLED, 0);
+        S->queue.clear();
+        S->cv_work.notify_all();
+        S->cv_done.notify_all();
+    }
+    if (S->worker.joinable()) S->worker.join();
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(S->device);
+    for (Request *r : S->active) {
+        if (r->g) release_graph(r->g, S->stream);
+        r->g = nullptr;
+    }
+    void *bufs[] = {S->dgraphs, S->tiles, S->warps, S->djobs, S->queue_state};
+    for (void *p : bufs)
+        if (p) dev_free(p, S->stream);
+    cudaStreamSynchronize(S->stream);
+    if (S->host_totals) cudaFreeHost(S->host_totals);
+    cudaStreamDestroy(S->stream);
+    cudaSetDevice(prev);
+    for (auto &kv : S->all) delete kv.second;
+    delete S;
+}
+
+}  // extern "C"

@@ -124,41 +124,84 @@ class SignedBipartite:
         return int(self.u.shape[0])
 
 
+class _InverseCdf:
+    """searchsorted(cdf, r, side="right") for many r at once, through a table of bucket
+    starts: bucket b = floor(r * 2^22) holds the answer between tab[b] and tab[b + 1], so
+    a few vectorised bisection steps finish it. The result equals numpy's searchsorted."""
+
+    BITS = 22
+
+    def __init__(self, cdf: np.ndarray):
+        self.cdf = cdf
+        k = 1 << self.BITS
+        self.tab = np.searchsorted(cdf, np.arange(k + 1, dtype=np.float64) / k, side="right")
+
+    def __call__(self, r: np.ndarray) -> np.ndarray:
+        b = (r * (1 << self.BITS)).astype(np.int64)
+        lo = self.tab[b]
+        hi = self.tab[b + 1]
+        n = self.cdf.shape[0]
+        while True:
+            open_ = lo < hi
+            if not open_.any():
+                return lo
+            mid = (lo + hi) >> 1
+            go = np.zeros(lo.shape, dtype=bool)
+            m = open_
+            go[m] = self.cdf[np.minimum(mid[m], n - 1)] <= r[m]
+            lo = np.where(m & go, mid + 1, lo)
+            hi = np.where(m & ~go, mid, hi)
+
+
 def _draw_distinct_pairs(seed: int, n_u: int, n_v: int, n_edges: int,
                          cdf_u: np.ndarray | None, cdf_v: np.ndarray | None) -> np.ndarray:
-    """First ``n_edges`` distinct pairs (as keys u * n_v + v) in draw order, then sorted."""
+    """First ``n_edges`` distinct pairs (as keys u * n_v + v) in draw order, then sorted.
+
+    Draws come in rounds; each round's keys are de-duplicated among themselves (first
+    occurrence wins) and against the pairs already kept, so the result is the same as
+    scanning the whole draw sequence once.
+    """
     if n_edges > n_u * n_v:
         raise ValueError("more edges than vertex pairs")
-    keys_parts: list[np.ndarray] = []
+    # the bucket table pays off only for many draws over a long table
+    big = n_edges >= (1 << 20)
+    inv_u = (_InverseCdf(cdf_u) if big else (lambda r: np.searchsorted(cdf_u, r, side="right"))) \
+        if cdf_u is not None else None
+    inv_v = (_InverseCdf(cdf_v) if big else (lambda r: np.searchsorted(cdf_v, r, side="right"))) \
+        if cdf_v is not None else None
+    kept = np.empty(0, dtype=np.int64)      # sorted distinct keys so far
     drawn = 0
-    have = np.empty(0, dtype=np.int64)
-    while True:
-        need = n_edges - have.shape[0]
-        if need <= 0:
-            break
-        batch = max(int(need * 1.15) + 1024, 4096)
+    fresh_ratio = 1.0                        # sizes the next round; does not change the result
+    while kept.shape[0] < n_edges:
+        need = n_edges - kept.shape[0]
+        batch = max(int(need * 1.15 / max(fresh_ratio, 0.02)) + 1024, 4096)
         ru = uniform01(seed, TAG_U, drawn, batch)
         rv = uniform01(seed, TAG_V, drawn, batch)
         if cdf_u is None:
             uu = np.minimum((ru * n_u).astype(np.int64), n_u - 1)
         else:
-            uu = np.minimum(np.searchsorted(cdf_u, ru, side="right"), n_u - 1).astype(np.int64)
+            uu = np.minimum(inv_u(ru), n_u - 1).astype(np.int64)
         if cdf_v is None:
             vv = np.minimum((rv * n_v).astype(np.int64), n_v - 1)
         else:
-            vv = np.minimum(np.searchsorted(cdf_v, rv, side="right"), n_v - 1).astype(np.int64)
+            vv = np.minimum(inv_v(rv), n_v - 1).astype(np.int64)
         drawn += batch
-        keys_parts.append(uu * n_v + vv)
-        allk = np.concatenate(keys_parts)
-        keys_parts = [allk]
-        uniq, first = np.unique(allk, return_index=True)
-        if uniq.shape[0] >= n_edges:
-            order = np.sort(first)[:n_edges]
-            have = np.sort(allk[order])
-            break
-        have = uniq
-        # keep the raw draw order list (keys_parts) and continue drawing
-    return have
+        keys = uu * n_v + vv
+        uniq, first = np.unique(keys, return_index=True)
+        if kept.shape[0]:
+            pos = np.searchsorted(kept, uniq)
+            pos[pos == kept.shape[0]] = 0
+            fresh = kept[pos] != uniq
+            uniq, first = uniq[fresh], first[fresh]
+        fresh_ratio = uniq.shape[0] / batch
+        if uniq.shape[0] > need:
+            # keep the fresh keys whose first draw comes before the need-th fresh first draw
+            is_first = np.zeros(batch, dtype=bool)
+            is_first[first] = True
+            cutoff = int(np.searchsorted(np.cumsum(is_first), need))  # draw index of the need-th
+            uniq = uniq[first <= cutoff]
+        kept = np.insert(kept, np.searchsorted(kept, uniq), uniq) if kept.shape[0] else uniq
+    return kept
 
 
 def _cdf(w: np.ndarray) -> np.ndarray:
@@ -295,3 +338,26 @@ WORKLOADS = {
     "powerlaw_1m_200k_20m": powerlaw_1m_200k,
     "hubs_50k_2m_100m": hubs_50k_2m,
 }
+
+
+def _batch_worker(spec: BatchGraphSpec) -> SignedBipartite:
+    return batch_graph(spec)
+
+
+def batch_graphs(specs: list[BatchGraphSpec], workers: int | None = None) -> list[SignedBipartite]:
+    """Generates many batch members, in a pool of worker processes when workers > 1.
+
+    The pool uses the 'spawn' start method, so it is safe in processes that already
+    initialised CUDA. Every graph is a pure function of its spec, so the result does not
+    depend on the number of workers.
+    """
+    import os
+
+    workers = workers if workers is not None else min(16, os.cpu_count() or 1)
+    if workers <= 1 or len(specs) < 8:
+        return [batch_graph(s) for s in specs]
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_batch_worker, specs, chunksize=max(1, len(specs) // (4 * workers))))

@@ -1,0 +1,152 @@
+"""GPU tests of the batched form (bbc_count_batch, bbc_autotune_batch) and the serving
+loop (bbc_server_*): every count must equal the oracle's / the single-graph count exactly.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_17707_gb300 import bbc, synth
+from tests import _golden
+
+pytestmark = pytest.mark.gpu
+
+
+def small_batch(n, seed, e_max=20_000):
+    specs = synth.batch_specs(n, seed=seed, e_max=e_max)
+    return [synth.batch_graph(s) for s in specs]
+
+
+@pytest.fixture(scope="module")
+def batch_graphs():
+    gs = small_batch(48, seed=3)
+    gs.append(synth.SignedBipartite(10, 12, np.zeros(0, np.int32), np.zeros(0, np.int32),
+                                    np.zeros(0, np.int8)))
+    gs.append(synth.SignedBipartite(1, 300, np.zeros(300, np.int32), np.arange(300, dtype=np.int32),
+                                    np.ones(300, np.int8)))
+    gs.append(synth.powerlaw_1m_200k(seed=2, scale=0.005))
+    want = [oracle.count(g, threads=4, per_vertex=False).balanced for g in gs]
+    return gs, want
+
+
+def test_batch_matches_oracle_and_replays(gpu_lib, batch_graphs):
+    gs, want = batch_graphs
+    G = [bbc.Graph.from_synthetic(g) for g in gs]
+    try:
+        got = bbc.count_batch(G)
+        assert got == want
+        assert bbc.count_batch(G) == want          # replay of the captured plan
+        single = [h.count()[0] for h in G]
+        assert single == want
+    finally:
+        for h in G:
+            h.free()
+
+
+def test_batch_tunings_and_autotune_agree(gpu_lib, batch_graphs):
+    gs, want = batch_graphs
+    G = [bbc.Graph.from_synthetic(g) for g in gs]
+    try:
+        for kw in (dict(tile_words=1024, warp_max_wedges=1), dict(warp_max_wedges=512),
+                   dict(blocks_per_sm=1), dict(tile_words=4096, split_wedges=200)):
+            t = bbc.default_tuning()
+            for k, v in kw.items():
+                setattr(t, k, v)
+            assert bbc.count_batch(G, tuning=t) == want
+        best = bbc.autotune_batch(G)
+        assert best.tile_words >= 0 and best.blocks_per_sm in (1, 2)
+        assert bbc.count_batch(G) == want           # now served with the tuned choice
+        assert bbc.count_batch(G, tuning=best) == want
+    finally:
+        for h in G:
+            h.free()
+
+
+def test_batch_of_one_and_of_none(gpu_lib):
+    g = synth.uniform_2k_3k(seed=1)
+    G = bbc.Graph.from_synthetic(g)
+    try:
+        assert bbc.count_batch([G]) == [oracle.count(g, per_vertex=False).balanced]
+        assert bbc.count_batch([]) == []
+    finally:
+        G.free()
+
+
+# ------------------------------------------------------------------ serving
+
+def test_serving_results_equal_alone_and_in_the_mix(gpu_lib):
+    gs = small_batch(120, seed=9)
+    gs.insert(7, synth.powerlaw_1m_200k(seed=5, scale=0.02))   # a large request mid-stream
+    gs.insert(60, synth.hubs_50k_2m(seed=4, scale=0.002))
+    alone = []
+    for g in gs:
+        G = bbc.Graph.from_synthetic(g)
+        alone.append(G.count()[0])
+        G.free()
+    srv = bbc.Server(8 << 30)
+    try:
+        tickets = [srv.submit(g) for g in gs]
+        got = [srv.wait(t, timeout_s=120.0) for t in tickets]
+        assert got == alone
+        st = srv.stats()
+        assert st["completed"] == len(gs)
+        assert 0 < st["p50_us"] <= st["p99_us"]
+        # a finished ticket can be polled again
+        assert srv.poll(tickets[0]) == alone[0]
+    finally:
+        srv.close()
+
+
+def test_serving_errors_stay_with_their_request(gpu_lib):
+    lib = gpu_lib
+    srv = bbc.Server(8 << 30)
+    try:
+        ok = synth.uniform_graph(200, 150, 3000, 0.6, seed=1)
+        bad = _golden.graph(3, 3, [(0, 0, 1), (5, 1, 1)])          # id out of range
+        t_ok1 = srv.submit(ok)
+        t_bad = srv.submit(bad)
+        t_ok2 = srv.submit(ok)
+        want = oracle.count(ok, per_vertex=False).balanced
+        assert srv.wait(t_ok1, 60.0) == want
+        with pytest.raises(bbc.BBCError) as e:
+            srv.wait(t_bad, 60.0)
+        assert e.value.status == 2
+        assert srv.wait(t_ok2, 60.0) == want
+        b = ctypes.c_uint64()
+        assert lib.bbc_poll(srv._h, 987654321, ctypes.byref(b)) == 1     # unknown ticket
+    finally:
+        srv.close()
+
+
+def test_serving_budget_and_bounded_waits(gpu_lib):
+    lib = gpu_lib
+    small = bbc.Server(4 << 20)
+    try:
+        big = synth.uniform_graph(3000, 3000, 200_000, 0.5, seed=2)
+        with pytest.raises(bbc.BBCError) as e:
+            small.submit(big)
+        assert e.value.status == 7
+    finally:
+        small.close()
+    srv = bbc.Server(8 << 30)
+    try:
+        g = synth.powerlaw_1m_200k(seed=7, scale=0.05)
+        t = srv.submit(g)
+        b = ctypes.c_uint64()
+        st = lib.bbc_wait(srv._h, t, 0, ctypes.byref(b))
+        assert st in (0, 9)                                          # done, or timed out
+        assert srv.wait(t, 120.0) == oracle.count(g, threads=8, per_vertex=False).balanced
+    finally:
+        srv.close()
+
+
+def test_serving_shutdown_cancels_queued_requests(gpu_lib):
+    srv = bbc.Server(8 << 30)
+    gs = small_batch(40, seed=12)
+    for g in gs:
+        srv.submit(g)
+    srv.close()   # must return with requests still queued or in flight
