@@ -33,6 +33,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -199,6 +201,105 @@ def bench_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_batched(args, dev):
+    """The batched workload: 4,096 Chung-Lu graphs counted by one replay of a captured CUDA
+    graph (autotuned) against per-graph launches of the single-graph path."""
+    import torch
+
+    from paper_2601_17707_gb300 import bbc, synth
+
+    t0 = time.perf_counter()
+    specs = synth.batch_specs(4096, seed=0)
+    gs = synth.batch_graphs(specs)
+    gen_s = time.perf_counter() - t0
+    G = [bbc.Graph.from_synthetic(g) for g in gs]
+    W = sum(h.info().wedges for h in G)
+    E = sum(g.n_edges for g in gs)
+    stream = torch.cuda.current_stream(dev)
+    tuned = bbc.autotune_batch(G)
+    ref = bbc.count_batch(G)                 # builds and caches the plan for the tuned choice
+    for _ in range(2):
+        bbc.count_batch(G)
+    torch.cuda.synchronize(dev)
+    reps = max(3, args.steps)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        got = bbc.count_batch(G)
+    t_batch = (time.perf_counter() - t0) / reps
+    exact = got == ref
+    # per-graph launches on one stream with one sync at the end: the plain kernel
+    # (static one-block-per-anchor schedule) and, for context, the work-queue kernel
+    totals = torch.empty(2 * len(G), dtype=torch.int64, device=dev)
+
+    def per_graph(tuning):
+        for i, h in enumerate(G):
+            h.count_async(totals[2 * i:2 * i + 2], tuning=tuning)
+        torch.cuda.synchronize(dev)
+        best = 1e30
+        for _ in range(2):
+            t0 = time.perf_counter()
+            for i, h in enumerate(G):
+                h.count_async(totals[2 * i:2 * i + 2], tuning=tuning)
+            torch.cuda.synchronize(dev)
+            best = min(best, time.perf_counter() - t0)
+        single = totals.view(-1, 2)[:, 0].cpu().numpy().view(np.uint64).tolist()
+        return best, [int(x) for x in single] == ref
+
+    plain = bbc.default_tuning()
+    plain.plain = 1
+    t_per, ok1 = per_graph(plain)
+    t_per_q, ok2 = per_graph(None)
+    exact = exact and ok1 and ok2
+    for h in G:
+        h.free()
+    return {"workload": "batch_4096_chung_lu", "graphs": len(G), "edges": E, "wedges": W,
+            "graphs_per_s": len(G) / t_batch, "wedges_per_s": W / t_batch,
+            "ms_per_batch": 1e3 * t_batch,
+            "per_graph_plain_graphs_per_s": len(G) / t_per, "per_graph_plain_ms": 1e3 * t_per,
+            "speedup_vs_per_graph_plain": t_per / t_batch,
+            "per_graph_queue_graphs_per_s": len(G) / t_per_q, "per_graph_queue_ms": 1e3 * t_per_q,
+            "speedup_vs_per_graph_queue": t_per_q / t_batch,
+            "counts_identical": bool(exact), "tuning": tuned.as_dict(),
+            "timing": f"host wall clock around bbc_count_batch (replay + D2H + sync), mean of "
+                      f"{reps}; per-graph: bbc_count_async per graph on one stream, one sync "
+                      "(plain = static one-block-per-anchor kernel; queue = work-queue kernel)",
+            "generation_s": gen_s}, gs
+
+
+def bench_serving(args, pool):
+    """Poisson arrivals at several offered rates; 99% of requests from the batch pool,
+    1% large (|U| = 200,000, |V| = 100,000, 5M edges); 8 GB device budget."""
+    from paper_2601_17707_gb300 import bbc, synth
+
+    large = synth.large_serving_graph(seed=0)
+    rng = np.random.default_rng(0)
+    out = []
+    for rate in args.serve_rates:
+        n = int(min(args.serve_max_requests, max(200, rate * args.serve_seconds)))
+        srv = bbc.Server(8 << 30)
+        gaps = rng.exponential(1.0 / rate, size=n)
+        picks = rng.integers(0, len(pool), size=n)
+        is_large = rng.random(n) < 0.01
+        tickets = []
+        t_start = time.perf_counter()
+        t_next = t_start
+        for k in range(n):
+            t_next += gaps[k]
+            while time.perf_counter() < t_next:
+                pass
+            g = large if is_large[k] else pool[picks[k]]
+            tickets.append(srv.submit(g))
+        for t in tickets:
+            srv.wait(t, timeout_s=600.0)
+        wall = time.perf_counter() - t_start
+        st = srv.stats()
+        srv.close()
+        out.append({"offered_graphs_per_s": rate, "requests": n, "large": int(is_large.sum()),
+                    "graphs_per_s": n / wall, "p50_ms": st["p50_us"] / 1e3,
+                    "p99_ms": st["p99_us"] / 1e3, "mean_ms": st["mean_us"] / 1e3})
+    return {"budget_gb": 8, "latency": "submit to completion, library clock", "rates": out}
+
+
 def bench_gpu(args):
     import torch
 
@@ -304,6 +405,12 @@ def bench_gpu(args):
                 "kernel_ms_per_launch": tile_ms / tile_launches,
                 "algorithmic_bytes_per_launch": alg_bytes}
 
+    batched = serving = None
+    if not args.no_batched:
+        batched, pool = bench_batched(args, dev)
+        if not args.no_serve:
+            serving = bench_serving(args, pool)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, w, dt, threads, stride = oracle_sample(g, args.cpu_seconds)
@@ -324,6 +431,7 @@ def bench_gpu(args):
                        "parallelism": f"replicas x{world}", "balanced": b_last},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": launches, "kernel_profile": prof,
+            "batched": batched, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -339,6 +447,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-batched", action="store_true", help="skip the 4,096-graph batch")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving sweep")
+    ap.add_argument("--serve-rates", type=float, nargs="+",
+                    default=[100, 300, 1000, 3000, 10000, 20000])
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-max-requests", type=int, default=3000)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -66,15 +66,18 @@ typedef struct bbc_server bbc_server;
  * never depend on these values, only the speed does.
  */
 typedef struct bbc_tuning {
-    int32_t tile_words;        /* endpoint counters per shared-memory tile (<= 53,248) */
+    int32_t tile_words;        /* 32-bit words per shared-memory counter tile (0: the
+                                  largest that keeps blocks_per_sm blocks resident) */
     int32_t warp_max_wedges;   /* anchors with at most this many oriented wedges go to the
                                   one-warp hash path (<= 512) */
-    int32_t dense_min_permille;/* other anchors use dense tiles when wedges/span >= this/1000,
-                                  else the block hash path */
+    int32_t dense_min_permille;/* reserved for a block-level hash path (unused) */
     int32_t split_wedges;      /* anchors with more wedges than this are split into
                                   tile-range items that run on different blocks */
     int32_t blocks_per_sm;     /* resident blocks per SM of the tile kernel (1 or 2) */
-    int32_t reserved[3];
+    int32_t plain;             /* 1: the static schedule of G-BBC (Algorithm 3) -- one block
+                                  per anchor in rank order, no work queue, no heavy-first
+                                  ordering, no hash path, no splitting; for comparisons */
+    int32_t reserved[2];
 } bbc_tuning;
 
 /* Fills *t with the built-in defaults. */

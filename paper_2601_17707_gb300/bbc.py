@@ -58,7 +58,8 @@ class Tuning(ctypes.Structure):
         ("dense_min_permille", ctypes.c_int32),
         ("split_wedges", ctypes.c_int32),
         ("blocks_per_sm", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("plain", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
     def as_dict(self) -> dict:

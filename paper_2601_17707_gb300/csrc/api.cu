@@ -153,7 +153,9 @@ Tuning resolve_tuning(const bbc_tuning *t, int sm_count) {
     r.dense_min_permille = 0;
     r.split_wedges = 0;  // 0: chosen per launch from the total work
     r.blocks_per_sm = 2;
+    r.plain = 0;
     if (t) {
+        r.plain = t->plain ? 1 : 0;
         if (t->blocks_per_sm == 1 || t->blocks_per_sm == 2) r.blocks_per_sm = t->blocks_per_sm;
         if (t->tile_words > 0) r.tile_words = t->tile_words;
         if (t->warp_max_wedges > 0) r.warp_max_wedges = t->warp_max_wedges;
@@ -184,6 +186,10 @@ bbc_status count_graph(bbc_graph *g, uint64_t *totals_dev, uint64_t *per_u, uint
                        const bbc_tuning *tuning, cudaStream_t st) {
     Tuning T = resolve_tuning(tuning, device_sm_count());
     if (T.split_wedges == 0) T.split_wedges = auto_split(g->wedges, device_sm_count(), T.blocks_per_sm);
+    if (T.plain) {
+        T.warp_max_wedges = 0;
+        T.split_wedges = (long long)1 << 62;
+    }
     BBC_TRY(build_work_lists(g, T, st));
     const bool pv = per_u || per_v;
     if (pv && !g->bS) {
@@ -268,6 +274,7 @@ bbc_status bbc_tuning_default(bbc_tuning *t) {
     t->dense_min_permille = r.dense_min_permille;
     t->split_wedges = 0;
     t->blocks_per_sm = r.blocks_per_sm;
+    t->plain = 0;
     return BBC_OK;
 }
 

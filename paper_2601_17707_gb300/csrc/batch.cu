@@ -118,7 +118,8 @@ std::vector<long long> shape_key(int32_t n, bbc_graph *const *gs) {
 
 bool same_tuning(const Tuning &a, const Tuning &b) {
     return a.tile_words == b.tile_words && a.warp_max_wedges == b.warp_max_wedges &&
-           a.split_wedges == b.split_wedges && a.blocks_per_sm == b.blocks_per_sm;
+           a.split_wedges == b.split_wedges && a.blocks_per_sm == b.blocks_per_sm &&
+           a.plain == b.plain;
 }
 
 #define BBC_LAUNCH_OK(what)                                        \
@@ -325,6 +326,10 @@ Tuning batch_tuning(int32_t n, bbc_graph *const *gs, const bbc_tuning *t) {
         uint64_t w = 0;
         for (int i = 0; i < n; ++i) w += gs[i]->wedges;
         T.split_wedges = auto_split(w, device_sm_count(), T.blocks_per_sm);
+    }
+    if (T.plain) {
+        T.warp_max_wedges = 0;
+        T.split_wedges = (long long)1 << 62;
     }
     return T;
 }

@@ -82,6 +82,7 @@ struct Tuning {
     int dense_min_permille;
     long long split_wedges;
     int blocks_per_sm;
+    int plain;                 // static one-block-per-anchor schedule (Algorithm 3)
 };
 
 Tuning resolve_tuning(const bbc_tuning *t, int sm_count);

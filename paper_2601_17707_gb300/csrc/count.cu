@@ -568,7 +568,7 @@ __device__ void run_tile_item(const DevGraph &G, const TileItem &item, int tile_
 // Persistent blocks pop (anchor, tile range) items, heaviest first.
 __global__ void __launch_bounds__(kTileThreads, 2)
 k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, int n_items,
-       unsigned *head, int tile_words) {
+       unsigned *head, int tile_words, int static_schedule) {
     extern __shared__ uint4 smem_tile[];
     uint32_t *tile = reinterpret_cast<uint32_t *>(smem_tile);
     __shared__ ChunkSmem cs;
@@ -576,8 +576,16 @@ k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, 
     __shared__ unsigned long long s_red[2][kTileWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < tile_words; i += blockDim.x) tile[i] = 0;
+    int next_static = blockIdx.x;
     for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
+        if (threadIdx.x == 0) {
+            if (static_schedule) {
+                s_item = next_static;
+                next_static += gridDim.x;
+            } else {
+                s_item = (int)atomicAdd(head, 1u);
+            }
+        }
         __syncthreads();
         const int it = s_item;
         if (it >= n_items) break;
@@ -703,8 +711,10 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
     if (L.n_tile_items > 0) {
         const int tok = profile_begin(kProfTile, st);
         note_launch();
-        k_tile<<<sms * T.blocks_per_sm, kTileThreads, (size_t)T.tile_words * 4, st>>>(
-            L.graphs, L.tile_items, L.n_tile_items, &L.queue->tile_head, T.tile_words);
+        // work-queue schedule: persistent blocks; plain schedule: one block per item
+        const int grid = T.plain ? L.n_tile_items : sms * T.blocks_per_sm;
+        k_tile<<<grid, kTileThreads, (size_t)T.tile_words * 4, st>>>(
+            L.graphs, L.tile_items, L.n_tile_items, &L.queue->tile_head, T.tile_words, T.plain);
         BBC_CUDA_TRY(cudaGetLastError());
         profile_end(tok, st);
     }
@@ -725,7 +735,7 @@ bbc_status launch_tile_only(const DevGraph *graphs, const TileItem *items, int n
     if (n_items <= 0) return BBC_OK;
     note_launch();
     k_tile<<<blocks, kTileThreads, (size_t)tile_words * 4, st>>>(graphs, items, n_items, head,
-                                                                 tile_words);
+                                                                 tile_words, 0);
     BBC_CUDA_TRY(cudaGetLastError());
     return BBC_OK;
 }

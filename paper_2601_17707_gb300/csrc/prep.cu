@@ -395,7 +395,7 @@ bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
     }
     if (g->items_valid && g->items_tuning.tile_words == t.tile_words &&
         g->items_tuning.warp_max_wedges == t.warp_max_wedges &&
-        g->items_tuning.split_wedges == t.split_wedges)
+        g->items_tuning.split_wedges == t.split_wedges && g->items_tuning.plain == t.plain)
         return BBC_OK;
     if (g->tile_items) dev_free(g->tile_items, st);
     if (g->warp_items) dev_free(g->warp_items, st);
@@ -443,8 +443,12 @@ bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
     k_emit_items<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, pt, ph, raw, keys,
                                                      g->warp_items);
     BBC_LAUNCH_CHECK("k_emit_items");
-    // Order the tile items by expected cost, largest first.
-    if (ntile > 0) {
+    // Order the tile items by expected cost, largest first (the plain schedule keeps
+    // rank order).
+    if (ntile > 0 && t.plain) {
+        BBC_CUDA_TRY(cudaMemcpyAsync(g->tile_items, raw, sizeof(TileItem) * (size_t)ntile,
+                                     cudaMemcpyDeviceToDevice, st));
+    } else if (ntile > 0) {
         uint32_t *order = nullptr;
         BBC_TRY(sc.get(&order, (size_t)ntile));
         note_launch();

@@ -81,7 +81,8 @@ def test_random_graphs_all_paths(gpu_lib, seed):
     # default tuning, dense tiles only, hash only where possible, many tiny tiles and
     # splits, one block per SM, both orientations and both pair sides
     for t in (None, tuning(warp_max_wedges=1), tuning(warp_max_wedges=512),
-              tuning(tile_words=1024, split_wedges=64), tuning(blocks_per_sm=1, tile_words=53248)):
+              tuning(tile_words=1024, split_wedges=64), tuning(blocks_per_sm=1, tile_words=53248),
+              tuning(plain=1), tuning(plain=1, tile_words=1024)):
         assert_parity(g, tuning=t, want=want)
     for flags in (bbc.ORIENT_LOW_ANCHOR, bbc.SIDE_FORCE_U, bbc.SIDE_FORCE_V,
                   bbc.SIDE_FORCE_V | bbc.ORIENT_LOW_ANCHOR):
@@ -100,6 +101,7 @@ def test_power_law_shape_scaled(gpu_lib, scale):
     want = oracle.count(g, threads=8)
     assert_parity(g, want=want)
     assert_parity(g, tuning=tuning(tile_words=2048), want=want)
+    assert_parity(g, tuning=tuning(plain=1), want=want)
     assert_parity(g, flags=bbc.ORIENT_LOW_ANCHOR, want=want)
 
 
