@@ -24,6 +24,8 @@
 // counters: the pair {a, w} adds f = C(p,2) + C(n,2) to both b(a) and b(w); and a wedge
 // a - c - w of type t lies in (count_t(a, w) - 1) balanced butterflies through c, so a
 // second sweep over the same slices, after the counters are complete, adds that to b(c).
+#include <type_traits>
+
 #include "graph.cuh"
 
 namespace bbc {
@@ -288,9 +290,23 @@ __device__ __forceinline__ int last_le(const uint32_t *p, uint32_t k) {
     return lo;
 }
 
+// Per-wedge work. MODE 1 sums (count - 1); with 8- and 16-bit counters a thread's or a
+// piece's sum stays far below 2^32 (at most 1,024 wedges of count <= 65,535), so it is
+// kept in 32 bits; 32-bit counters use 64-bit sums.
+template <int CW>
+using Acc = typename std::conditional<CW == 2, unsigned long long, uint32_t>::type;
+
+__device__ __forceinline__ uint32_t warp_sum32(uint32_t x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
+}
+__device__ __forceinline__ unsigned long long warp_sum_acc(unsigned long long x) { return warp_sum(x); }
+__device__ __forceinline__ uint32_t warp_sum_acc(uint32_t x) { return warp_sum32(x); }
+
 template <int MODE, int CW>
 __device__ __forceinline__ void wedge(const TileCounter<CW> &ctr, uint32_t x, uint32_t sg,
-                                      unsigned long long &acc) {
+                                      Acc<CW> &acc) {
     const uint32_t t = (x ^ sg) >> 31;
     if (MODE == 0)
         ctr.bump(x & kIdMask, t);
@@ -349,6 +365,22 @@ __device__ __forceinline__ void find_slice(const DevGraph &G, int64_t e, const S
     len = en - b;
 }
 
+// Adds a chunk-centre's per-tile sum into the chunk accumulator (cs.acc, read as 32-bit
+// words for 8- and 16-bit counters: a centre's sum over one tile is at most 25,176
+// endpoints times 65,534 < 2^32).
+template <int CW>
+__device__ __forceinline__ void acc_add(ChunkSmem &cs, int j, Acc<CW> v) {
+    if (CW == 2)
+        atomicAdd(cs.acc + j, (unsigned long long)v);
+    else
+        atomicAdd(reinterpret_cast<uint32_t *>(cs.acc) + j, (uint32_t)v);
+}
+
+template <int CW>
+__device__ __forceinline__ unsigned long long acc_get(ChunkSmem &cs, int j) {
+    return CW == 2 ? cs.acc[j] : (unsigned long long)reinterpret_cast<uint32_t *>(cs.acc)[j];
+}
+
 // One pass of the whole block over the oriented wedges of anchor rows [sb, se) whose
 // endpoints lie in [X.lo, X.hi), in chunks of kChunk centres. Per chunk, every thread
 // finds its centre's slice; slices shorter than kLongMin are concatenated and cut into
@@ -358,7 +390,8 @@ __device__ __forceinline__ void find_slice(const DevGraph &G, int64_t e, const S
 // per-vertex sum. A single-chunk MODE 1 pass reuses the slices MODE 0 just found.
 template <int MODE, int CW>
 __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const SweepCtx &X,
-                            const TileCounter<CW> &ctr, ChunkSmem &cs) {
+                            const TileCounter<CW> &ctr, ChunkSmem &cs,
+                            unsigned long long &centre_carry) {
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t *__restrict__ rowC = G.rowC;
     for (int64_t cb = sb; cb < se; cb += kChunk) {
@@ -415,11 +448,11 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
                 uint32_t nb = cs.pshort[j + 1];
                 uint32_t base = cs.start[j] - cs.pshort[j];
                 uint32_t sg = cs.ent[j] & kSignBit;
-                unsigned long long acc = 0;
+                Acc<CW> acc = 0;
                 for (; k < k1; ++k) {
                     if (k >= nb) {
                         if (MODE == 1 && acc) {
-                            atomicAdd(cs.acc + j, acc);
+                            acc_add<CW>(cs, j, acc);
                             acc = 0;
                         }
                         do {
@@ -431,7 +464,7 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
                     }
                     wedge<MODE>(ctr, __ldg(rowC + (uint32_t)(base + k)), sg, acc);
                 }
-                if (MODE == 1 && acc) atomicAdd(cs.acc + j, acc);
+                if (MODE == 1 && acc) acc_add<CW>(cs, j, acc);
             }
         }
         // long slices: pieces pulled by warps
@@ -446,7 +479,7 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
                 const uint32_t n = min((uint32_t)kPiece, cs.len[j] - off);
                 const uint32_t s = cs.start[j] + off;
                 const uint32_t sg = cs.ent[j] & kSignBit;
-                unsigned long long acc = 0;
+                Acc<CW> acc = 0;
                 const uint32_t head = min(n, (4u - (s & 3u)) & 3u);
                 if ((uint32_t)lane < head) wedge<MODE>(ctr, __ldg(rowC + s + lane), sg, acc);
                 const uint32_t m4 = (n - head) >> 2;
@@ -461,13 +494,19 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
                 const uint32_t rest = (n - head) & 3u;
                 if ((uint32_t)lane < rest) wedge<MODE>(ctr, __ldg(rowC + s + head + 4 * m4 + lane), sg, acc);
                 if (MODE == 1) {
-                    acc = warp_sum(acc);
-                    if (lane == 0 && acc) atomicAdd(cs.acc + j, acc);
+                    acc = warp_sum_acc(acc);
+                    if (lane == 0 && acc) acc_add<CW>(cs, j, acc);
                 }
             }
         }
         __syncthreads();
-        if (MODE == 1 && ci < se && cs.acc[tid]) atomicAdd(G.bC + (ent & kIdMask), cs.acc[tid]);
+        if (MODE == 1 && ci < se) {
+            const unsigned long long mine = acc_get<CW>(cs, tid);
+            if (X.single)
+                centre_carry += mine;   // flushed once per item
+            else if (mine)
+                atomicAdd(G.bC + (ent & kIdMask), mine);
+        }
     }
 }
 
@@ -549,20 +588,22 @@ __device__ void run_tile_item(const DevGraph &G, const TileItem &item, int tile_
     const int nt_all = (int)((X.range_hi - X.range_lo + ept - 1) / ept);
     X.single = se - sb <= kChunk;
     X.use_cur = !X.single && G.cur != nullptr && t0 == 0 && t1 == nt_all;
+    unsigned long long centre_carry = 0;   // single chunk: this thread's centre, all tiles
     for (int t = t0; t < t1; ++t) {
         X.lo = X.range_lo + (uint32_t)t * ept;
         X.hi = min(X.lo + ept, X.range_hi);
         X.carry = t > t0;
         const TileCounter<CW> ctr{tile, X.lo};
         X.last_pass = G.bC == nullptr;
-        block_sweep<0>(G, sb, se, X, ctr, cs);
+        block_sweep<0>(G, sb, se, X, ctr, cs, centre_carry);
         if (G.bC) {
             X.last_pass = true;
-            block_sweep<1>(G, sb, se, X, ctr, cs);
+            block_sweep<1>(G, sb, se, X, ctr, cs, centre_carry);
         }
         tile_epilogue<CW>(tile, X.lo, X.hi, G.bS, bal, unb);
         __syncthreads();
     }
+    if (centre_carry) atomicAdd(G.bC + (cs.ent[threadIdx.x] & kIdMask), centre_carry);
 }
 
 // Persistent blocks pop (anchor, tile range) items, heaviest first.

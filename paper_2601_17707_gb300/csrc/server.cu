@@ -1,12 +1,14 @@
 // server.cu -- the serving loop of include/bbc.h (bbc_server_*, bbc_submit, bbc_poll,
 // bbc_wait): continuous batching of many graph-counting requests on one GPU.
 //
-// Requests are copied at submit time and queued. A worker thread runs ticks:
+// Requests are copied at submit time and queued. Then:
 //   1. admission: queued requests are admitted in arrival order while the device memory
 //      reserved for admitted requests plus theirs stays within the budget;
-//   2. newly admitted requests are prepared (bbc_prepare's pipeline) on the server's
-//      stream and their counts zeroed; their device layout stays resident until done;
-//   3. one launch of the counting kernels covers every admitted graph: all remaining work
+//   2. a pool of preparation threads, each on its own stream, prepares admitted requests
+//      (bbc_prepare's pipeline) and zeroes their counts; their device layout stays
+//      resident until done;
+// and a tick thread repeats:
+//   3. one launch of the counting kernels covers every prepared graph: all remaining work
 //      items of the small ones and a bounded chunk of each large one, so a large request
 //      advances over several ticks (its partial totals stay in device memory between
 //      ticks) and never holds small requests back for long;
@@ -29,6 +31,7 @@ namespace bbc {
 namespace {
 
 using Clock = std::chrono::steady_clock;
+constexpr int kPrepThreads = 6;     // preparation threads per server
 
 struct Request {
     uint64_t ticket = 0;
@@ -70,8 +73,12 @@ struct bbc_server {
     int device = 0;
     cudaStream_t stream = nullptr;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<bbc::Request *> queue;
+    std::condition_variable cv_work, cv_done, cv_prep;
+    std::deque<bbc::Request *> queue;      // submitted, not admitted
+    std::deque<bbc::Request *> to_prepare; // admitted
+    std::vector<bbc::Request *> ready;     // prepared, not yet counting
+    int preparing = 0;
+    std::vector<std::thread> preppers;
     std::vector<bbc::Request *> active;
     std::unordered_map<uint64_t, bbc::Request *> all;
     size_t reserved = 0;
@@ -109,29 +116,64 @@ void finish_locked(bbc_server *S, Request *r, bbc_status st, uint64_t balanced) 
             std::chrono::duration<double, std::micro>(r->t_done - r->t_submit).count());
 }
 
-// Prepares one admitted request; on failure the request completes with that status.
-bool admit_one(bbc_server *S, Request *r) {
-    bbc_graph *g = nullptr;
-    bbc_status st = prepare_graph(r->n_u, r->n_v, r->n_edges, r->u.data(), r->v.data(),
-                                  r->s.data(), 0u, S->stream, &g);
-    if (st == BBC_OK) st = build_work_lists(g, S->tuning, S->stream);
-    if (st == BBC_OK) {
-        cudaError_t e = cudaMemsetAsync(g->totals, 0, 16, S->stream);
-        if (e != cudaSuccess) st = cuda_fail(e, "server totals");
+// Moves queued requests to the preparation queue while their reservations fit.
+void admit_locked(bbc_server *S) {
+    bool any = false;
+    while (!S->queue.empty() && S->reserved + S->queue.front()->reserve <= S->budget) {
+        Request *r = S->queue.front();
+        S->queue.pop_front();
+        S->reserved += r->reserve;
+        S->to_prepare.push_back(r);
+        any = true;
     }
-    if (st != BBC_OK) {
-        if (g) release_graph(g, S->stream);
+    if (any) S->cv_prep.notify_all();
+}
+
+// A preparation thread: prepares admitted requests on its own stream, waits for that
+// stream, and hands the graph to the tick thread. A failed request completes with its
+// status and releases its reservation.
+void prep_main(bbc_server *S) {
+    cudaSetDevice(S->device);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    for (;;) {
+        Request *r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_prep.wait(lk, [&] { return S->stop || !S->to_prepare.empty(); });
+            if (S->stop) break;
+            r = S->to_prepare.front();
+            S->to_prepare.pop_front();
+            S->preparing++;
+        }
+        bbc_graph *g = nullptr;
+        bbc_status s = prepare_graph(r->n_u, r->n_v, r->n_edges, r->u.data(), r->v.data(),
+                                     r->s.data(), 0u, st, &g);
+        if (s == BBC_OK) s = build_work_lists(g, S->tuning, st);
+        if (s == BBC_OK) {
+            cudaError_t e = cudaMemsetAsync(g->totals, 0, 16, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) s = cuda_fail(e, "server preparation");
+        }
         std::lock_guard<std::mutex> lk(S->mu);
-        S->reserved -= r->reserve;
-        finish_locked(S, r, st, 0);
-        S->cv_done.notify_all();
-        return false;
+        S->preparing--;
+        if (s != BBC_OK) {
+            if (g) release_graph(g, st);
+            S->reserved -= r->reserve;
+            finish_locked(S, r, s, 0);
+            admit_locked(S);
+            S->cv_done.notify_all();
+        } else {
+            r->g = g;
+            r->u = {};
+            r->v = {};
+            r->s = {};
+            S->ready.push_back(r);
+            S->cv_work.notify_one();
+        }
     }
-    r->g = g;
-    r->u = {};
-    r->v = {};
-    r->s = {};
-    return true;
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
 }
 
 // One tick over the active requests: a combined work list and one counting launch.
@@ -200,25 +242,13 @@ bbc_status run_tick(bbc_server *S, std::vector<Request *> &act) {
 void worker_main(bbc_server *S) {
     cudaSetDevice(S->device);
     for (;;) {
-        std::vector<Request *> admitted;
-        {
-            std::unique_lock<std::mutex> lk(S->mu);
-            S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty() || !S->active.empty(); });
-            if (S->stop) break;
-            while (!S->queue.empty() && S->reserved + S->queue.front()->reserve <= S->budget) {
-                Request *r = S->queue.front();
-                S->queue.pop_front();
-                S->reserved += r->reserve;
-                admitted.push_back(r);
-            }
-        }
-        std::vector<Request *> fresh;
-        for (Request *r : admitted)
-            if (admit_one(S, r)) fresh.push_back(r);
         std::vector<Request *> act;
         {
-            std::lock_guard<std::mutex> lk(S->mu);
-            for (Request *r : fresh) S->active.push_back(r);
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_work.wait(lk, [&] { return S->stop || !S->ready.empty() || !S->active.empty(); });
+            if (S->stop) break;
+            for (Request *r : S->ready) S->active.push_back(r);
+            S->ready.clear();
             act = S->active;
         }
         if (act.empty()) continue;
@@ -238,6 +268,7 @@ void worker_main(bbc_server *S) {
             }
         }
         S->active = still;
+        admit_locked(S);
         S->cv_done.notify_all();
     }
 }
@@ -266,6 +297,7 @@ bbc_status bbc_server_create(size_t device_budget_bytes, const bbc_tuning *tunin
             return cuda_fail(e, "bbc_server_create stream");
         }
         S->worker = std::thread(worker_main, S);
+        for (int i = 0; i < kPrepThreads; ++i) S->preppers.emplace_back(prep_main, S);
         *out = S;
         return BBC_OK;
     } catch (...) {
@@ -304,7 +336,7 @@ bbc_status bbc_submit(bbc_server *S, int32_t n_u, int32_t n_v, int64_t n_edges, 
         S->all[r->ticket] = r;
         S->queue.push_back(r);
         *ticket = r->ticket;
-        S->cv_work.notify_one();
+        admit_locked(S);
         return BBC_OK;
     } catch (...) {
         set_error("bbc_submit: host allocation failed");
@@ -378,16 +410,27 @@ void bbc_server_destroy(bbc_server *S) {
         S->stop = true;
         for (Request *r : S->queue) finish_locked(S, r, BBC_E_CANCELLED, 0);
         S->queue.clear();
+        for (Request *r : S->to_prepare) finish_locked(S, r, BBC_E_CANCELLED, 0);
+        S->to_prepare.clear();
         S->cv_work.notify_all();
+        S->cv_prep.notify_all();
         S->cv_done.notify_all();
     }
     if (S->worker.joinable()) S->worker.join();
+    for (std::thread &t : S->preppers)
+        if (t.joinable()) t.join();
+    for (Request *r : S->ready) {
+        if (r->g) release_graph(r->g, S->stream);
+        r->g = nullptr;
+        finish_locked(S, r, BBC_E_CANCELLED, 0);
+    }
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(S->device);
     for (Request *r : S->active) {
         if (r->g) release_graph(r->g, S->stream);
         r->g = nullptr;
+        if (!r->done) finish_locked(S, r, BBC_E_CANCELLED, 0);
     }
     void *bufs[] = {S->dgraphs, S->tiles, S->warps, S->djobs, S->queue_state};
     for (void *p : bufs)
