@@ -204,7 +204,7 @@ bbc_status count_graph(bbc_graph *g, uint64_t *totals_dev, uint64_t *per_u, uint
     BBC_CUDA_TRY(cudaMemsetAsync(g->totals, 0, 16, st));
     BBC_CUDA_TRY(cudaMemsetAsync(g->queue, 0, sizeof(QueueState), st));
     static_assert(sizeof(DevGraph) % 8 == 0, "descriptor layout");
-    DevGraph d = host_descriptor(g, pv);
+    DevGraph d = host_descriptor(g, pv, true);
     note_launch();
     k_store_descriptor<<<1, 1, 0, st>>>(d, g->dgraph);
     BBC_CUDA_TRY(cudaGetLastError());

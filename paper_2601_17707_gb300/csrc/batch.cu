@@ -63,6 +63,7 @@ __global__ void k_gather_tile_items(const TileItem *__restrict__ in, const uint3
 
 struct Plan {
     std::vector<uint64_t> uids;
+    std::vector<uint64_t> versions;   // each graph's layout_version when the plan was built
     Tuning tuning{};
     int device = 0;
     int32_t n = 0;
@@ -144,6 +145,7 @@ bbc_status build_plan(int32_t n, bbc_graph *const *gs, const Tuning &T, std::uni
             return BBC_E_INVALID_ARG;
         }
         BBC_TRY(build_work_lists(gs[i], T, st));
+        P->versions.push_back(gs[i]->layout_version);
     }
     std::vector<DevGraph> hd(n);
     std::vector<CopyJob> jt, jh;
@@ -151,7 +153,7 @@ bbc_status build_plan(int32_t n, bbc_graph *const *gs, const Tuning &T, std::uni
     BBC_TRY(dev_alloc_n(&P->totals, (size_t)2 * n, st));
     for (int i = 0; i < n; ++i) {
         bbc_graph *g = gs[i];
-        hd[i] = host_descriptor(g, false);
+        hd[i] = host_descriptor(g, false, true);
         hd[i].totals = P->totals + 2 * i;
         if (g->n_tile) jt.push_back(CopyJob{g->tile_items, nt, g->n_tile, i});
         if (g->n_warp) jh.push_back(CopyJob{g->warp_items, nh, g->n_warp, i});
@@ -259,7 +261,8 @@ Plan *find_or_build(int32_t n, bbc_graph *const *gs, const Tuning &T, bbc_status
         Plan *p = g_plans[k].get();
         if (p->n != n || p->device != dev || !same_tuning(p->tuning, T)) continue;
         bool same = true;
-        for (int i = 0; i < n && same; ++i) same = p->uids[i] == gs[i]->uid;
+        for (int i = 0; i < n && same; ++i)
+            same = p->uids[i] == gs[i]->uid && p->versions[i] == gs[i]->layout_version;
         if (same) {
             auto keep = std::move(g_plans[k]);
             g_plans.erase(g_plans.begin() + (long)k);

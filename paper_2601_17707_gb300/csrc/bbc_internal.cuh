@@ -34,8 +34,10 @@ struct DevGraph {
     const unsigned long long *wl; // oriented wedges per anchor rank (orders work items)
     const uint2 *rng;          // per S -> C entry (a, c): the entries of row c that are
                                // endpoints of a, as an index range [x, y) into rowC
-    uint32_t *cur;             // per S -> C entry: slice cursor carried across tiles
-                               // (nullable: slices are then found by binary search)
+    const uint32_t *bnd;       // interior tile boundaries (nullable: found by search);
+                               // boundary t (1 <= t < tiles) of entry i of anchor a is
+                               // bnd[boff[a] + (t - 1) * degree(a) + i], an index into rowC
+    const int64_t *boff;
 };
 
 // A unit of work of the tile kernel: anchor `anchor` of graph `graph`, endpoint tiles
@@ -140,6 +142,7 @@ bbc_status radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, int bits,
 bbc_status exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n,
                                      cudaStream_t st);
 bbc_status exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t st);
+bbc_status exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t st);
 
 // ----------------------------------------------------------------------------- counting
 

@@ -35,7 +35,7 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kTileThreads = 512;
 constexpr int kTileWarps = kTileThreads / 32;
 constexpr int kChunk = kTileThreads;      // centres per block-sweep chunk
-constexpr int kLongMin = 256;             // slices this long are cut into pieces
+constexpr int kLongMin = 64;              // slices this long are cut into pieces
 constexpr int kPiece = 1024;              // wedges per piece of a long slice
 constexpr int kLongSlice = 64;            // warp sweep: slices this long use the whole warp
 constexpr int kHashThreads = 256;
@@ -338,29 +338,28 @@ __device__ __forceinline__ uint32_t gallop_rank(const uint32_t *__restrict__ row
 struct SweepCtx {
     uint32_t lo, hi;              // the tile's endpoint ranks [lo, hi)
     uint32_t range_lo, range_hi;  // the anchor's whole endpoint range
-    bool carry;                   // a previous tile of this item ended where this one starts
+    int t, nt;                    // this tile, and the anchor's number of tiles
+    int64_t bbase;                // boff[anchor]
+    int64_t deg;                  // the anchor's degree
     bool single;                  // all centres fit one chunk: slices stay in shared memory
-    bool use_cur;                 // multi-chunk anchor owned by this block: cursors in G.cur
-    bool last_pass;               // the last sweep over this tile (cursors advance after it)
 };
 
-// The slice of row c (entry e of the anchor's S -> C row) whose endpoint ranks lie in
-// [X.lo, X.hi). The anchor's whole range inside row c is known from preparation (rng), so
-// the first and last tiles need no search; other starts are carried from the previous
-// tile and other ends found by galloping.
-__device__ __forceinline__ void find_slice(const DevGraph &G, int64_t e, const SweepCtx &X,
-                                           uint32_t prev_end, bool have_prev, uint32_t &start,
-                                           uint32_t &len) {
+// The slice of row c (entry e, the i-th of the anchor's S -> C row) whose endpoint ranks
+// lie in [X.lo, X.hi). The anchor's whole range inside row c is known from preparation
+// (rng), so the first tile starts and the last ends there; interior boundaries come from
+// the table computed with the work lists (bnd), or, without it, from a binary search and
+// a gallop.
+__device__ __forceinline__ void find_slice(const DevGraph &G, int64_t e, int64_t i,
+                                           const SweepCtx &X, uint32_t &start, uint32_t &len) {
     const uint2 r = __ldg(G.rng + e);
-    const uint32_t rlo = r.x, rhi = r.y;
-    uint32_t b;
-    if (X.lo == X.range_lo)
-        b = rlo;
-    else if (have_prev)
-        b = prev_end;
-    else
-        b = (uint32_t)lower_bound_rank(G.rowC, rlo, rhi, X.lo);
-    const uint32_t en = X.hi >= X.range_hi ? rhi : gallop_rank(G.rowC, b, min(rhi, b + (X.hi - X.lo)), X.hi);
+    uint32_t b, en;
+    if (G.bnd) {
+        b = X.t == 0 ? r.x : __ldg(G.bnd + X.bbase + (int64_t)(X.t - 1) * X.deg + i);
+        en = X.t == X.nt - 1 ? r.y : __ldg(G.bnd + X.bbase + (int64_t)X.t * X.deg + i);
+    } else {
+        b = X.t == 0 ? r.x : (uint32_t)lower_bound_rank(G.rowC, r.x, r.y, X.lo);
+        en = X.t == X.nt - 1 ? r.y : gallop_rank(G.rowC, b, min(r.y, b + (X.hi - X.lo)), X.hi);
+    }
     start = b;
     len = en - b;
 }
@@ -406,17 +405,7 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
             uint32_t start = 0, len = 0;
             if (ci < se) {
                 ent = __ldg(G.rowS + ci);
-                uint32_t prev = 0;
-                bool have_prev = false;
-                if (X.carry && X.single) {
-                    prev = cs.start[tid] + cs.len[tid];
-                    have_prev = true;
-                } else if (X.carry && X.use_cur) {
-                    prev = G.cur[ci];
-                    have_prev = true;
-                }
-                find_slice(G, ci, X, prev, have_prev, start, len);
-                if (X.use_cur && X.last_pass) G.cur[ci] = start + len;
+                find_slice(G, ci, ci - sb, X, start, len);
             }
             const bool islong = len >= (uint32_t)kLongMin;
             const unsigned long long mine =
@@ -439,7 +428,8 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
             __syncthreads();
         }
         const uint32_t NS = cs.pshort[kChunk], NP = cs.ppiece[kChunk];
-        // short slices: contiguous equal shares
+        // short slices: contiguous equal shares, the next entry's load issued before the
+        // current entry's counter update
         if (NS) {
             uint32_t k = (uint32_t)(((unsigned long long)NS * tid) / kChunk);
             const uint32_t k1 = (uint32_t)(((unsigned long long)NS * (tid + 1)) / kChunk);
@@ -449,20 +439,34 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
                 uint32_t base = cs.start[j] - cs.pshort[j];
                 uint32_t sg = cs.ent[j] & kSignBit;
                 Acc<CW> acc = 0;
-                for (; k < k1; ++k) {
-                    if (k >= nb) {
-                        if (MODE == 1 && acc) {
-                            acc_add<CW>(cs, j, acc);
-                            acc = 0;
+                uint32_t x = __ldg(rowC + (uint32_t)(base + k));
+                for (;;) {
+                    const uint32_t k2 = k + 1;
+                    int j2 = j;
+                    uint32_t nb2 = nb, base2 = base, sg2 = sg, x2 = 0;
+                    if (k2 < k1) {
+                        if (k2 >= nb2) {
+                            do {
+                                ++j2;
+                                nb2 = cs.pshort[j2 + 1];
+                            } while (nb2 <= k2);
+                            base2 = cs.start[j2] - cs.pshort[j2];
+                            sg2 = cs.ent[j2] & kSignBit;
                         }
-                        do {
-                            ++j;
-                            nb = cs.pshort[j + 1];
-                        } while (nb <= k);
-                        base = cs.start[j] - cs.pshort[j];
-                        sg = cs.ent[j] & kSignBit;
+                        x2 = __ldg(rowC + (uint32_t)(base2 + k2));
                     }
-                    wedge<MODE>(ctr, __ldg(rowC + (uint32_t)(base + k)), sg, acc);
+                    wedge<MODE>(ctr, x, sg, acc);
+                    if (k2 >= k1) break;
+                    if (MODE == 1 && j2 != j && acc) {
+                        acc_add<CW>(cs, j, acc);
+                        acc = 0;
+                    }
+                    k = k2;
+                    j = j2;
+                    nb = nb2;
+                    base = base2;
+                    sg = sg2;
+                    x = x2;
                 }
                 if (MODE == 1 && acc) acc_add<CW>(cs, j, acc);
             }
@@ -484,12 +488,21 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
                 if ((uint32_t)lane < head) wedge<MODE>(ctr, __ldg(rowC + s + lane), sg, acc);
                 const uint32_t m4 = (n - head) >> 2;
                 const uint4 *v4 = reinterpret_cast<const uint4 *>(rowC + s + head);
-                for (uint32_t q = lane; q < m4; q += 32) {
-                    const uint4 x = __ldg(v4 + q);
-                    wedge<MODE>(ctr, x.x, sg, acc);
-                    wedge<MODE>(ctr, x.y, sg, acc);
-                    wedge<MODE>(ctr, x.z, sg, acc);
-                    wedge<MODE>(ctr, x.w, sg, acc);
+                // two 16-byte loads in flight per lane
+                for (uint32_t q = lane; q < m4; q += 64) {
+                    const uint4 xa = __ldg(v4 + q);
+                    const bool has_b = q + 32 < m4;
+                    const uint4 xb = has_b ? __ldg(v4 + q + 32) : make_uint4(0u, 0u, 0u, 0u);
+                    wedge<MODE>(ctr, xa.x, sg, acc);
+                    wedge<MODE>(ctr, xa.y, sg, acc);
+                    wedge<MODE>(ctr, xa.z, sg, acc);
+                    wedge<MODE>(ctr, xa.w, sg, acc);
+                    if (has_b) {
+                        wedge<MODE>(ctr, xb.x, sg, acc);
+                        wedge<MODE>(ctr, xb.y, sg, acc);
+                        wedge<MODE>(ctr, xb.z, sg, acc);
+                        wedge<MODE>(ctr, xb.w, sg, acc);
+                    }
                 }
                 const uint32_t rest = (n - head) & 3u;
                 if ((uint32_t)lane < rest) wedge<MODE>(ctr, __ldg(rowC + s + head + 4 * m4 + lane), sg, acc);
@@ -585,21 +598,18 @@ __device__ void run_tile_item(const DevGraph &G, const TileItem &item, int tile_
     X.range_lo = G.orient_low ? 0u : (uint32_t)a + 1u;
     X.range_hi = G.orient_low ? (uint32_t)a : (uint32_t)G.nS;
     const int t0 = item.tile_begin, t1 = tile_end_of(item);
-    const int nt_all = (int)((X.range_hi - X.range_lo + ept - 1) / ept);
+    X.nt = (int)((X.range_hi - X.range_lo + ept - 1) / ept);
     X.single = se - sb <= kChunk;
-    X.use_cur = !X.single && G.cur != nullptr && t0 == 0 && t1 == nt_all;
+    X.deg = se - sb;
+    X.bbase = G.boff ? G.boff[a] : 0;
     unsigned long long centre_carry = 0;   // single chunk: this thread's centre, all tiles
     for (int t = t0; t < t1; ++t) {
+        X.t = t;
         X.lo = X.range_lo + (uint32_t)t * ept;
         X.hi = min(X.lo + ept, X.range_hi);
-        X.carry = t > t0;
         const TileCounter<CW> ctr{tile, X.lo};
-        X.last_pass = G.bC == nullptr;
         block_sweep<0>(G, sb, se, X, ctr, cs, centre_carry);
-        if (G.bC) {
-            X.last_pass = true;
-            block_sweep<1>(G, sb, se, X, ctr, cs, centre_carry);
-        }
+        if (G.bC) block_sweep<1>(G, sb, se, X, ctr, cs, centre_carry);
         tile_epilogue<CW>(tile, X.lo, X.hi, G.bS, bal, unb);
         __syncthreads();
     }
@@ -783,6 +793,6 @@ bbc_status launch_tile_only(const DevGraph *graphs, const TileItem *items, int n
 
 // An upper bound of the tile kernel's static shared memory (checked against the
 // compiled kernel when the kernels are configured).
-int tile_static_smem_bytes() { return (int)sizeof(ChunkSmem) + 512; }
+int tile_static_smem_bytes() { return (int)sizeof(ChunkSmem) + 16 * kTileWarps + 512; }
 
 }  // namespace bbc

@@ -24,7 +24,10 @@ struct bbc_graph {
     int32_t *permC = nullptr;
     unsigned long long *wl = nullptr;  // oriented wedges per anchor rank
     uint2 *rng = nullptr;      // per S -> C entry (a, c): a's endpoint range [x, y) in rowC
-    uint32_t *cur = nullptr;   // per S -> C entry: slice cursor of the tile kernel (scratch)
+    uint32_t *anchor_of = nullptr;  // per S -> C entry: its anchor's rank
+    uint32_t *bnd = nullptr;   // interior tile boundaries for the current work lists
+    int64_t *boff = nullptr;   // nS + 1 offsets into bnd
+    uint64_t layout_version = 0;    // bumped whenever the work lists are rebuilt
 
     // work lists (rebuilt when the tuning changes)
     bbc::Tuning items_tuning{};
@@ -51,6 +54,8 @@ bbc_status prepare_graph(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_
                          bbc_graph **out);
 bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st);
 void release_graph(bbc_graph *g, cudaStream_t st);
-DevGraph host_descriptor(const bbc_graph *g, bool per_vertex);
+// The kernels' view of g. with_bounds: the tile boundaries of the work lists last
+// built (pass true only right after build_work_lists with the tuning being launched).
+DevGraph host_descriptor(const bbc_graph *g, bool per_vertex, bool with_bounds = false);
 
 }  // namespace bbc

@@ -263,13 +263,58 @@ __device__ __forceinline__ void classify_one(const ClassifyParams &P, unsigned l
 
 __global__ void k_classify(ClassifyParams P, const unsigned long long *__restrict__ wl,
                            const int64_t *__restrict__ rowS_off, int32_t *__restrict__ n_tile,
-                           int32_t *__restrict__ n_warp) {
+                           int32_t *__restrict__ n_warp, int64_t *__restrict__ n_bnd) {
     for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < P.nS;
          a += (int64_t)gridDim.x * blockDim.x) {
         int kind, cw, nt, g;
-        classify_one(P, wl[a], rowS_off[a + 1] - rowS_off[a], (int)a, &kind, &cw, &nt, &g);
+        const int64_t deg = rowS_off[a + 1] - rowS_off[a];
+        classify_one(P, wl[a], deg, (int)a, &kind, &cw, &nt, &g);
         n_tile[a] = kind == 2 ? g : 0;
         n_warp[a] = kind == 1 ? 1 : 0;
+        n_bnd[a] = kind == 2 && nt > 1 ? deg * (nt - 1) : 0;
+    }
+}
+
+// Interior tile boundaries: for every S -> C entry (a, c) of a tile anchor, the index in
+// row c of the first endpoint of each of a's tiles 1 .. tiles-1, found by galloping from
+// the previous boundary. One thread per entry; the layout (boundary-major per anchor)
+// lets the tile kernel read them coalesced.
+__global__ void k_tile_bounds(ClassifyParams P, const unsigned long long *__restrict__ wl,
+                              const int64_t *__restrict__ rowS_off,
+                              const uint32_t *__restrict__ anchor_of, const uint2 *__restrict__ rng,
+                              const uint32_t *__restrict__ rowC, const int64_t *__restrict__ boff,
+                              int64_t n, uint32_t *__restrict__ bnd) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = anchor_of[e];
+        const int64_t sb = rowS_off[a], deg = rowS_off[a + 1] - sb;
+        int kind, cw, nt, g;
+        classify_one(P, wl[a], deg, (int)a, &kind, &cw, &nt, &g);
+        if (kind != 2 || nt <= 1) continue;
+        const uint32_t ept = cw == 0 ? 2u * (uint32_t)P.tile_words
+                                     : (cw == 1 ? (uint32_t)P.tile_words : (uint32_t)P.tile_words / 2u);
+        const uint32_t range_lo = P.orient_low ? 0u : a + 1u;
+        const uint2 r = rng[e];
+        uint32_t pos = r.x;
+        uint32_t *dst = bnd + boff[a] + (e - sb);
+        for (int t = 1; t < nt; ++t) {
+            const uint32_t key = range_lo + (uint32_t)t * ept;
+            uint32_t lo = pos, step = 1;
+            while (lo + step <= r.y && (__ldg(rowC + lo + step - 1) & kIdMask) < key) {
+                lo += step;
+                step <<= 1;
+            }
+            uint32_t hi = min(lo + step - 1, r.y);
+            while (lo < hi) {
+                const uint32_t m = (lo + hi) >> 1;
+                if ((__ldg(rowC + m) & kIdMask) < key)
+                    lo = m + 1;
+                else
+                    hi = m;
+            }
+            pos = lo;
+            dst[(int64_t)(t - 1) * deg] = pos;
+        }
     }
 }
 
@@ -360,7 +405,7 @@ bbc_status rank_side(const int32_t *deg, int64_t n, int32_t maxdeg, int32_t *ran
 
 }  // namespace
 
-DevGraph host_descriptor(const bbc_graph *g, bool per_vertex) {
+DevGraph host_descriptor(const bbc_graph *g, bool per_vertex, bool with_bounds) {
     DevGraph d{};
     d.rowS_off = g->rowS_off;
     d.rowS = g->rowS;
@@ -374,13 +419,14 @@ DevGraph host_descriptor(const bbc_graph *g, bool per_vertex) {
     d.totals = g->totals;
     d.wl = g->wl;
     d.rng = g->rng;
-    d.cur = g->cur;
+    d.bnd = with_bounds ? g->bnd : nullptr;
+    d.boff = with_bounds ? g->boff : nullptr;
     return d;
 }
 
 void release_graph(bbc_graph *g, cudaStream_t st) {
     if (!g) return;
-    void *ptrs[] = {g->rowS_off, g->rowS, g->rowC_off, g->rowC, g->permS, g->permC, g->wl, g->rng, g->cur,
+    void *ptrs[] = {g->rowS_off, g->rowS, g->rowC_off, g->rowC, g->permS, g->permC, g->wl, g->rng, g->anchor_of, g->bnd, g->boff,
                     g->tile_items, g->warp_items, g->dgraph, g->bS, g->bC,
                     g->totals, g->queue};
     for (void *p : ptrs)
@@ -389,20 +435,21 @@ void release_graph(bbc_graph *g, cudaStream_t st) {
 }
 
 bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
-    if (!g->cur && g->n_edges > 0) {
-        BBC_TRY(dev_alloc_n(&g->cur, (size_t)g->n_edges, st));
-        g->device_bytes += (size_t)g->n_edges * 4;
-    }
     if (g->items_valid && g->items_tuning.tile_words == t.tile_words &&
         g->items_tuning.warp_max_wedges == t.warp_max_wedges &&
         g->items_tuning.split_wedges == t.split_wedges && g->items_tuning.plain == t.plain)
         return BBC_OK;
     if (g->tile_items) dev_free(g->tile_items, st);
     if (g->warp_items) dev_free(g->warp_items, st);
+    if (g->bnd) dev_free(g->bnd, st);
+    if (g->boff) dev_free(g->boff, st);
     g->tile_items = nullptr;
     g->warp_items = nullptr;
+    g->bnd = nullptr;
+    g->boff = nullptr;
     g->n_tile = g->n_warp = 0;
     g->items_valid = false;
+    g->layout_version++;
     const int64_t nS = g->nS;
     if (nS == 0) {
         g->items_tuning = t;
@@ -411,21 +458,32 @@ bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
     }
     Scratch sc(st);
     int32_t *nt = nullptr, *nh = nullptr;
-    int64_t *pt = nullptr, *ph = nullptr;
+    int64_t *pt = nullptr, *ph = nullptr, *nb = nullptr;
     BBC_TRY(sc.get(&nt, (size_t)nS));
     BBC_TRY(sc.get(&nh, (size_t)nS));
     BBC_TRY(sc.get(&pt, (size_t)nS + 1));
     BBC_TRY(sc.get(&ph, (size_t)nS + 1));
+    BBC_TRY(sc.get(&nb, (size_t)nS));
+    BBC_TRY(dev_alloc_n(&g->boff, (size_t)nS + 1, st));
     ClassifyParams P{g->nS, g->orient_low, t.tile_words, t.warp_max_wedges, t.split_wedges};
     note_launch();
-    k_classify<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, nt, nh);
+    k_classify<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, nt, nh, nb);
     BBC_LAUNCH_CHECK("k_classify");
     BBC_TRY(exclusive_scan_i32_to_i64(nt, pt, nS, st));
     BBC_TRY(exclusive_scan_i32_to_i64(nh, ph, nS, st));
-    int64_t counts[2];
+    BBC_TRY(exclusive_scan_i64(nb, g->boff, nS, st));
+    int64_t counts[3];
     BBC_CUDA_TRY(cudaMemcpyAsync(&counts[0], pt + nS, 8, cudaMemcpyDeviceToHost, st));
     BBC_CUDA_TRY(cudaMemcpyAsync(&counts[1], ph + nS, 8, cudaMemcpyDeviceToHost, st));
+    BBC_CUDA_TRY(cudaMemcpyAsync(&counts[2], g->boff + nS, 8, cudaMemcpyDeviceToHost, st));
     BBC_CUDA_TRY(cudaStreamSynchronize(st));
+    BBC_TRY(dev_alloc_n(&g->bnd, (size_t)counts[2], st));
+    if (counts[2] > 0 && g->n_edges > 0) {
+        note_launch();
+        k_tile_bounds<<<grid_for(g->n_edges), kThreads, 0, st>>>(
+            P, g->wl, g->rowS_off, g->anchor_of, g->rng, g->rowC, g->boff, g->n_edges, g->bnd);
+        BBC_LAUNCH_CHECK("k_tile_bounds");
+    }
     if (counts[0] > INT32_MAX || counts[1] > INT32_MAX) {
         set_error("work list longer than 2^31 items");
         return BBC_E_INVALID_ARG;
@@ -582,7 +640,8 @@ bbc_status prepare_graph(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_
     // 4. the two CSR arrays
     const int64_t E = n_edges;
     uint32_t *kA = nullptr, *vA = nullptr, *kB = nullptr, *vB = nullptr;
-    BBC_TRY(sc.get(&kA, (size_t)E));
+    BBC_TRY(dev_alloc_n(&kA, (size_t)E, st));   // becomes g->anchor_of after the sort
+    g->anchor_of = kA;
     BBC_TRY(dev_alloc_n(&vA, (size_t)E, st));
     g->rowS = vA;
     BBC_TRY(sc.get(&kB, (size_t)E));
@@ -664,7 +723,7 @@ bbc_status prepare_graph(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_
     BBC_TRY(dev_alloc_n(&g->totals, 2, st));
     BBC_TRY(dev_alloc_n(&g->queue, 1, st));
     BBC_TRY(dev_alloc_n(&g->dgraph, 1, st));
-    g->device_bytes = (size_t)(nS + 1 + nC + 1) * 8 + (size_t)E * 16 + (size_t)(nS + nC) * 4 +
+    g->device_bytes = (size_t)(nS + 1 + nC + 1) * 8 + (size_t)E * 20 + (size_t)(nS + nC) * 4 +
                       (size_t)nS * 8;
     *out = g;
     guard.g = nullptr;

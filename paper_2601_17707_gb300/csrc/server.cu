@@ -187,7 +187,7 @@ bbc_status run_tick(bbc_server *S, std::vector<Request *> &act) {
     std::vector<int32_t> take_t(n), take_h(n);
     for (size_t i = 0; i < n; ++i) {
         bbc_graph *g = act[i]->g;
-        hd[i] = host_descriptor(g, false);
+        hd[i] = host_descriptor(g, false, true);
         const int32_t rt = g->n_tile - act[i]->tile_done;
         const int32_t rh = g->n_warp - act[i]->warp_done;
         take_t[i] = std::min(rt, chunk);

@@ -211,6 +211,10 @@ bbc_status exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n,
     return exclusive_scan<int32_t, int64_t>(in, out, n, st);
 }
 
+bbc_status exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t st) {
+    return exclusive_scan<int64_t, int64_t>(in, out, n, st);
+}
+
 bbc_status exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t st) {
     return exclusive_scan<uint32_t, uint32_t>(in, out, n, st);
 }
