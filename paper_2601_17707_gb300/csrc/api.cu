@@ -89,7 +89,7 @@ struct ProfSlot {
     bool used = false;
 };
 std::vector<ProfSlot> g_prof;
-const char *const kProfNames[kProfKinds] = {"k_tile", "k_warp_hash"};
+const char *const kProfNames[kProfKinds] = {"k_tile", "k_warp_hash", "k_warp_tile"};
 }  // namespace
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -214,6 +214,8 @@ bbc_status count_graph(bbc_graph *g, uint64_t *totals_dev, uint64_t *per_u, uint
     L.n_tile_items = g->n_tile;
     L.warp_items = g->warp_items;
     L.n_warp_items = g->n_warp;
+    L.wt_items = g->wt_items;
+    L.n_wt_items = g->n_wt;
     L.queue = g->queue;
     L.tuning = T;
     BBC_TRY(launch_count(L, st));

@@ -73,14 +73,15 @@ struct Plan {
     QueueState *queue = nullptr;
     TileItem *tiles = nullptr;
     HashItem *warp = nullptr;
-    int32_t n_tile = 0, n_warp = 0;
+    HashItem *wt = nullptr;
+    int32_t n_tile = 0, n_warp = 0, n_wt = 0;
     cudaStream_t stream = nullptr;            // capture / replay stream
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t exec = nullptr;
 
     ~Plan() {
         if (exec) cudaGraphExecDestroy(exec);
-        void *ps[] = {dgraphs, totals, queue, tiles, warp};
+        void *ps[] = {dgraphs, totals, queue, tiles, warp, wt};
         for (void *p : ps)
             if (p) dev_free(p, stream);
         if (stream) cudaStreamSynchronize(stream);
@@ -148,8 +149,8 @@ bbc_status build_plan(int32_t n, bbc_graph *const *gs, const Tuning &T, std::uni
         P->versions.push_back(gs[i]->layout_version);
     }
     std::vector<DevGraph> hd(n);
-    std::vector<CopyJob> jt, jh;
-    int64_t nt = 0, nh = 0;
+    std::vector<CopyJob> jt, jh, jw;
+    int64_t nt = 0, nh = 0, nw = 0;
     BBC_TRY(dev_alloc_n(&P->totals, (size_t)2 * n, st));
     for (int i = 0; i < n; ++i) {
         bbc_graph *g = gs[i];
@@ -157,30 +158,34 @@ bbc_status build_plan(int32_t n, bbc_graph *const *gs, const Tuning &T, std::uni
         hd[i].totals = P->totals + 2 * i;
         if (g->n_tile) jt.push_back(CopyJob{g->tile_items, nt, g->n_tile, i});
         if (g->n_warp) jh.push_back(CopyJob{g->warp_items, nh, g->n_warp, i});
+        if (g->n_wt) jw.push_back(CopyJob{g->wt_items, nw, g->n_wt, i});
         nt += g->n_tile;
         nh += g->n_warp;
+        nw += g->n_wt;
     }
-    if (nt > INT32_MAX || nh > INT32_MAX) {
+    if (nt > INT32_MAX || nh > INT32_MAX || nw > INT32_MAX) {
         set_error("bbc_count_batch: too many work items");
         return BBC_E_INVALID_ARG;
     }
     P->n_tile = (int32_t)nt;
     P->n_warp = (int32_t)nh;
+    P->n_wt = (int32_t)nw;
     BBC_TRY(dev_alloc_n(&P->dgraphs, (size_t)n, st));
     BBC_TRY(dev_alloc_n(&P->queue, 1, st));
     BBC_TRY(dev_alloc_n(&P->tiles, (size_t)nt, st));
     BBC_TRY(dev_alloc_n(&P->warp, (size_t)nh, st));
+    BBC_TRY(dev_alloc_n(&P->wt, (size_t)nw, st));
     BBC_CUDA_TRY(cudaMallocHost(&P->host_totals, sizeof(unsigned long long) * 2 * (size_t)std::max(n, 1)));
     BBC_CUDA_TRY(cudaMemcpyAsync(P->dgraphs, hd.data(), sizeof(DevGraph) * (size_t)n,
                                  cudaMemcpyHostToDevice, st));
     // concatenate, tagging each item with its graph index
     CopyJob *djobs = nullptr;
-    const size_t maxj = std::max(jt.size(), jh.size());
+    const size_t maxj = std::max(jt.size(), std::max(jh.size(), jw.size()));
     BBC_TRY(dev_alloc_n(&djobs, maxj, st));
     struct Part {
         std::vector<CopyJob> *jobs;
         int which;
-    } parts[2] = {{&jt, 0}, {&jh, 2}};
+    } parts[3] = {{&jt, 0}, {&jh, 2}, {&jw, 3}};
     bbc_status s = BBC_OK;
     for (auto &pt : parts) {
         if (pt.jobs->empty()) continue;
@@ -194,6 +199,7 @@ bbc_status build_plan(int32_t n, bbc_graph *const *gs, const Tuning &T, std::uni
         note_launch();
         if (pt.which == 0) k_concat_items<TileItem><<<nb, kThreads, 0, st>>>(djobs, P->tiles);
         if (pt.which == 2) k_concat_items<HashItem><<<nb, kThreads, 0, st>>>(djobs, P->warp);
+        if (pt.which == 3) k_concat_items<HashItem><<<nb, kThreads, 0, st>>>(djobs, P->wt);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // djobs is reused
         if (e != cudaSuccess) {
@@ -234,6 +240,8 @@ bbc_status build_plan(int32_t n, bbc_graph *const *gs, const Tuning &T, std::uni
     L.n_tile_items = P->n_tile;
     L.warp_items = P->warp;
     L.n_warp_items = P->n_warp;
+    L.wt_items = P->wt;
+    L.n_wt_items = P->n_wt;
     L.queue = P->queue;
     L.tuning = T;
     BBC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));

@@ -57,13 +57,21 @@ __host__ __device__ inline uint32_t pack_tile_end(int end, int cw) {
     return (uint32_t)end | ((uint32_t)cw << 30);
 }
 
-// A unit of work of the hash kernel: one anchor and its oriented wedge count.
+// A unit of work of the warp kernels: one anchor, its oriented wedge count, and (warp
+// tiles) its counter width code.
 struct HashItem {
     int32_t graph;
     int32_t anchor;
     int32_t wedges;
-    int32_t pad;
+    int32_t cw;
 };
+
+// Words of one warp's counter table in the warp-tile kernel, and the endpoints it holds
+// per counter width code.
+constexpr int kWtWords = 1536;
+__host__ __device__ constexpr uint32_t warp_tile_endpoints(int cw) {
+    return cw == 0 ? 2u * kWtWords : (cw == 1 ? (uint32_t)kWtWords : (uint32_t)kWtWords / 2u);
+}
 
 // Queue heads and the error word of the persistent kernels; zeroed before a launch.
 struct QueueState {
@@ -71,6 +79,7 @@ struct QueueState {
     unsigned int warp_head;    // hash items
     unsigned int spare;
     unsigned int error;        // nonzero: a kernel saw an impossible state (see kErr*)
+    unsigned int wt_head;      // warp-tile items
 };
 
 enum : unsigned int {
@@ -114,7 +123,7 @@ void note_launch();
 // Optional per-kernel timing (bbc_profile_start / bbc_profile_stop): while enabled, the
 // counting kernels are bracketed by CUDA events on their own stream. profile_begin
 // returns a token (-1 when profiling is off or the stream is being captured).
-enum { kProfTile = 0, kProfHash = 1, kProfKinds = 2 };
+enum { kProfTile = 0, kProfHash = 1, kProfWarpTile = 2, kProfKinds = 3 };
 int profile_begin(int kind, cudaStream_t st);
 void profile_end(int token, cudaStream_t st);
 
@@ -152,6 +161,8 @@ struct CountLaunch {
     int32_t n_tile_items;
     const HashItem *warp_items; // device
     int32_t n_warp_items;
+    const HashItem *wt_items;   // device, warp-tile items
+    int32_t n_wt_items;
     QueueState *queue;          // device, zeroed by the caller before the launch
     Tuning tuning;
 };
@@ -171,7 +182,7 @@ struct CopyJob {
 bbc_status concat_items(const std::vector<CopyJob> &jobs, bool tiles, void *dst, CopyJob *djobs,
                         cudaStream_t st);
 
-// Queues the counting kernels (dense tiles, then warp hash) on `st`.
+// Queues the counting kernels (block tiles, warp tiles, warp hash) on `st`.
 bbc_status launch_count(const CountLaunch &L, cudaStream_t st);
 
 // Launches only the tile kernel over `items` with `blocks` persistent blocks; touches no

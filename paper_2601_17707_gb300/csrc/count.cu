@@ -38,6 +38,8 @@ constexpr int kChunk = kTileThreads;      // centres per block-sweep chunk
 constexpr int kLongMin = 64;              // slices this long are cut into pieces
 constexpr int kPiece = 1024;              // wedges per piece of a long slice
 constexpr int kLongSlice = 64;            // warp sweep: slices this long use the whole warp
+constexpr int kWtThreads = 512;          // warp-tile kernel: 16 warps, one table each
+constexpr int kWtWarps = kWtThreads / 32;
 constexpr int kHashThreads = 256;
 constexpr int kHashWarps = kHashThreads / 32;
 constexpr int kHashSlots = 1024;          // per warp; holds anchors of <= 512 wedges
@@ -112,14 +114,13 @@ struct HashCounter {
 
 // ----------------------------------------------------------------------------- sweep
 
-// One warp's pass over the oriented wedges of anchor rows [sb, se) whose endpoints lie
-// in [lo, hi) (the hash kernel's sweep). MODE 0 bumps the counters; MODE 1 (the
+// One warp's pass over all oriented wedges of anchor rows [sb, se) (the warp kernels'
+// sweep: their anchors fit one counter table). MODE 0 bumps the counters; MODE 1 (the
 // per-vertex centre pass) reads them and adds (count - 1) per wedge to the centre's b.
 // The warp takes batches of 32 centres from *batch_ctr; lane j owns centre j's slice.
 template <int MODE, class Counter>
-__device__ __forceinline__ void warp_sweep(const DevGraph &G, int64_t sb, int64_t se, uint32_t lo,
-                                      uint32_t hi, const Counter &ctr, int *batch_ctr,
-                                      uint32_t *sacc) {
+__device__ __forceinline__ void warp_sweep(const DevGraph &G, int64_t sb, int64_t se,
+                                      const Counter &ctr, int *batch_ctr, uint32_t *sacc) {
     const int lane = threadIdx.x & 31;
     const int64_t nbatch = (se - sb + 31) >> 5;
     const uint32_t *__restrict__ rowC = G.rowC;
@@ -133,14 +134,13 @@ __device__ __forceinline__ void warp_sweep(const DevGraph &G, int64_t sb, int64_
         int len = 0;
         uint32_t sg = 0, c = 0;
         if (ci < se) {
+            // the whole endpoint range of the anchor inside row c (known from preparation)
             const uint32_t ent = __ldg(G.rowS + ci);
             c = ent & kIdMask;
             sg = ent & kSignBit;
-            const int64_t rb = __ldg(G.rowC_off + c), re = __ldg(G.rowC_off + c + 1);
-            const int64_t bb = lo == 0 ? rb : lower_bound_rank(rowC, rb, re, lo);
-            const int64_t ee = hi >= (uint32_t)G.nS ? re : lower_bound_rank(rowC, bb, re, hi);
-            b = bb;
-            len = (int)(ee - bb);
+            const uint2 r = __ldg(G.rng + ci);
+            b = r.x;
+            len = (int)(r.y - r.x);
         }
         // Long slices: the whole warp sweeps one slice at a time, coalesced.
         unsigned longm = __ballot_sync(kFull, len >= kLongSlice);
@@ -691,20 +691,18 @@ k_warp_hash(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ it
         const DevGraph &G = graphs[item.graph];
         const int a = item.anchor;
         const int64_t sb = G.rowS_off[a], se = G.rowS_off[a + 1];
-        const uint32_t lo = G.orient_low ? 0u : (uint32_t)a + 1u;
-        const uint32_t hi = G.orient_low ? (uint32_t)a : (uint32_t)G.nS;
         // table of 2^k >= 2 * wedges slots (at least 64)
         int lg = 6;
         while ((1 << lg) < 2 * item.wedges && lg < 10) ++lg;
         const HashCounter ctr{keys, vals, (1u << lg) - 1u, 32 - lg, &q->error};
         if (lane == 0) s_batch[warp] = 0;
         __syncwarp();
-        warp_sweep<0>(G, sb, se, lo, hi, ctr, &s_batch[warp], nullptr);
+        warp_sweep<0>(G, sb, se, ctr, &s_batch[warp], nullptr);
         __syncwarp();
         if (G.bC) {
             if (lane == 0) s_batch[warp] = 0;
             __syncwarp();
-            warp_sweep<1>(G, sb, se, lo, hi, ctr, &s_batch[warp], s_acc[warp]);
+            warp_sweep<1>(G, sb, se, ctr, &s_batch[warp], s_acc[warp]);
             __syncwarp();
         }
         unsigned long long bal = 0, unb = 0;
@@ -731,6 +729,89 @@ k_warp_hash(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ it
     }
 }
 
+
+// ----------------------------------------------------------------------------- warp tiles
+
+// One warp's dense counter table for an anchor whose whole endpoint range fits it
+// (single-tile anchors of small graphs): no block barrier, sixteen anchors in flight per
+// block.
+template <int CW>
+__device__ void warp_tile_item(const DevGraph &G, int a, uint32_t *tile, int *batch_ctr,
+                               uint32_t *sacc) {
+    const int lane = threadIdx.x & 31;
+    const int64_t sb = G.rowS_off[a], se = G.rowS_off[a + 1];
+    const uint32_t lo = G.orient_low ? 0u : (uint32_t)a + 1u;
+    const uint32_t hi = G.orient_low ? (uint32_t)a : (uint32_t)G.nS;
+    const TileCounter<CW> ctr{tile, lo};
+    if (lane == 0) *batch_ctr = 0;
+    __syncwarp();
+    warp_sweep<0>(G, sb, se, ctr, batch_ctr, nullptr);
+    __syncwarp();
+    if (G.bC) {
+        if (lane == 0) *batch_ctr = 0;
+        __syncwarp();
+        warp_sweep<1>(G, sb, se, ctr, batch_ctr, sacc);
+        __syncwarp();
+    }
+    const uint32_t n = hi - lo;
+    unsigned long long bal = 0, unb = 0;
+    if (CW == 2) {
+        for (uint32_t i = lane; i < n; i += 32) {
+            const uint32_t p = tile[2 * i], m = tile[2 * i + 1];
+            if ((p | m) == 0) continue;
+            tile[2 * i] = 0;
+            tile[2 * i + 1] = 0;
+            pair_total(p, m, G.bS, lo + i, bal, unb);
+        }
+    } else {
+        const uint32_t words = CW == 0 ? (n + 1) / 2 : n;
+        for (uint32_t i = lane; i < words; i += 32) {
+            const uint32_t x = tile[i];
+            if (x == 0) continue;
+            tile[i] = 0;
+            if (CW == 0) {
+                pair_total(x & 0xffu, (x >> 8) & 0xffu, G.bS, lo + 2 * i, bal, unb);
+                pair_total((x >> 16) & 0xffu, x >> 24, G.bS, lo + 2 * i + 1, bal, unb);
+            } else {
+                pair_total(x & 0xffffu, x >> 16, G.bS, lo + i, bal, unb);
+            }
+        }
+    }
+    bal = warp_sum(bal);
+    unb = warp_sum(unb);
+    if (lane == 0) {
+        if (bal) atomicAdd(G.totals + 0, bal);
+        if (unb) atomicAdd(G.totals + 1, unb);
+        if (G.bS && bal) atomicAdd(G.bS + a, bal);
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kWtThreads, 2)
+k_warp_tile(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ items, int n_items,
+            QueueState *q) {
+    extern __shared__ uint4 smem_wt[];
+    __shared__ uint32_t s_acc[kWtWarps][32];
+    __shared__ int s_batch[kWtWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *tile = reinterpret_cast<uint32_t *>(smem_wt) + warp * kWtWords;
+    for (int i = lane; i < kWtWords; i += 32) tile[i] = 0;
+    __syncwarp();
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = (int)atomicAdd(&q->wt_head, 1u);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= n_items) break;
+        const HashItem item = items[it];
+        const DevGraph &G = graphs[item.graph];
+        switch (item.cw) {
+            case 0: warp_tile_item<0>(G, item.anchor, tile, &s_batch[warp], s_acc[warp]); break;
+            case 1: warp_tile_item<1>(G, item.anchor, tile, &s_batch[warp], s_acc[warp]); break;
+            default: warp_tile_item<2>(G, item.anchor, tile, &s_batch[warp], s_acc[warp]); break;
+        }
+    }
+}
+
 }  // namespace
 
 bbc_status configure_count_kernels() {
@@ -750,6 +831,8 @@ bbc_status configure_count_kernels() {
                                           maxopt - (int)fa.sharedSizeBytes));
         BBC_CUDA_TRY(cudaFuncSetAttribute(k_warp_hash, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           kHashWarps * 2 * kHashSlots * 4));
+        BBC_CUDA_TRY(cudaFuncSetAttribute(k_warp_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          kWtWarps * kWtWords * 4));
         configured_device = dev;
     }
     return BBC_OK;
@@ -766,6 +849,14 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
         const int grid = T.plain ? L.n_tile_items : sms * T.blocks_per_sm;
         k_tile<<<grid, kTileThreads, (size_t)T.tile_words * 4, st>>>(
             L.graphs, L.tile_items, L.n_tile_items, &L.queue->tile_head, T.tile_words, T.plain);
+        BBC_CUDA_TRY(cudaGetLastError());
+        profile_end(tok, st);
+    }
+    if (L.n_wt_items > 0) {
+        const int tok = profile_begin(kProfWarpTile, st);
+        note_launch();
+        k_warp_tile<<<sms * 2, kWtThreads, kWtWarps * kWtWords * 4, st>>>(
+            L.graphs, L.wt_items, L.n_wt_items, L.queue);
         BBC_CUDA_TRY(cudaGetLastError());
         profile_end(tok, st);
     }

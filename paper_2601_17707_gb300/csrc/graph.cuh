@@ -36,6 +36,8 @@ struct bbc_graph {
     int32_t n_tile = 0;
     bbc::HashItem *warp_items = nullptr;
     int32_t n_warp = 0;
+    bbc::HashItem *wt_items = nullptr;
+    int32_t n_wt = 0;
 
     // count-time state
     bbc::DevGraph *dgraph = nullptr;       // device copy of the descriptor

@@ -230,9 +230,11 @@ struct ClassifyParams {
     int tile_words;
     int warp_max;
     long long split;
+    int warp_tiles;            // single-tile anchors that fit a warp's table go to k_warp_tile
 };
 
-// Work of one anchor: kind 0 none, 1 warp-hash item, 2 tile items; for tiles, the
+// Work of one anchor: kind 0 none, 1 warp-hash item, 2 tile items, 3 warp-tile item
+// (its whole endpoint range fits one warp's counter table); for tiles, the
 // counter width code (largest reachable count min(degree, wedges) <= 255 / 65535 / more),
 // the number of tiles over its endpoint range and how many items they are split into.
 __device__ __forceinline__ void classify_one(const ClassifyParams &P, unsigned long long wl,
@@ -259,11 +261,17 @@ __device__ __forceinline__ void classify_one(const ClassifyParams &P, unsigned l
     *cw = w;
     *ntiles = nt;
     *groups = (int)g;
+    if (P.warp_tiles && span <= (long long)warp_tile_endpoints(w)) {
+        *kind = 3;
+        *ntiles = 1;
+        *groups = 1;
+    }
 }
 
 __global__ void k_classify(ClassifyParams P, const unsigned long long *__restrict__ wl,
                            const int64_t *__restrict__ rowS_off, int32_t *__restrict__ n_tile,
-                           int32_t *__restrict__ n_warp, int64_t *__restrict__ n_bnd) {
+                           int32_t *__restrict__ n_warp, int64_t *__restrict__ n_bnd,
+                           int32_t *__restrict__ n_wt) {
     for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < P.nS;
          a += (int64_t)gridDim.x * blockDim.x) {
         int kind, cw, nt, g;
@@ -271,6 +279,7 @@ __global__ void k_classify(ClassifyParams P, const unsigned long long *__restric
         classify_one(P, wl[a], deg, (int)a, &kind, &cw, &nt, &g);
         n_tile[a] = kind == 2 ? g : 0;
         n_warp[a] = kind == 1 ? 1 : 0;
+        n_wt[a] = kind == 3 ? 1 : 0;
         n_bnd[a] = kind == 2 && nt > 1 ? deg * (nt - 1) : 0;
     }
 }
@@ -322,8 +331,9 @@ __global__ void k_tile_bounds(ClassifyParams P, const unsigned long long *__rest
 // expected wedge count, largest first (the fanout ordering of Algorithm 4).
 __global__ void k_emit_items(ClassifyParams P, const unsigned long long *__restrict__ wl,
                              const int64_t *__restrict__ rowS_off, const int64_t *__restrict__ pos_tile,
-                             const int64_t *__restrict__ pos_warp, TileItem *__restrict__ tiles,
-                             uint32_t *__restrict__ keys, HashItem *__restrict__ warp) {
+                             const int64_t *__restrict__ pos_warp, const int64_t *__restrict__ pos_wt,
+                             TileItem *__restrict__ tiles, uint32_t *__restrict__ keys,
+                             HashItem *__restrict__ warp, HashItem *__restrict__ wt) {
     for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < P.nS;
          a += (int64_t)gridDim.x * blockDim.x) {
         int kind, cw, nt, g;
@@ -331,6 +341,8 @@ __global__ void k_emit_items(ClassifyParams P, const unsigned long long *__restr
         classify_one(P, w, rowS_off[a + 1] - rowS_off[a], (int)a, &kind, &cw, &nt, &g);
         if (kind == 1) {
             warp[pos_warp[a]] = HashItem{0, (int32_t)a, (int32_t)w, 0};
+        } else if (kind == 3) {
+            wt[pos_wt[a]] = HashItem{0, (int32_t)a, (int32_t)(w > 0x7fffffffull ? 0x7fffffff : w), cw};
         } else if (kind == 2) {
             TileItem *dst = tiles + pos_tile[a];
             uint32_t *kd = keys + pos_tile[a];
@@ -427,7 +439,7 @@ DevGraph host_descriptor(const bbc_graph *g, bool per_vertex, bool with_bounds) 
 void release_graph(bbc_graph *g, cudaStream_t st) {
     if (!g) return;
     void *ptrs[] = {g->rowS_off, g->rowS, g->rowC_off, g->rowC, g->permS, g->permC, g->wl, g->rng, g->anchor_of, g->bnd, g->boff,
-                    g->tile_items, g->warp_items, g->dgraph, g->bS, g->bC,
+                    g->tile_items, g->warp_items, g->wt_items, g->dgraph, g->bS, g->bC,
                     g->totals, g->queue};
     for (void *p : ptrs)
         if (p) dev_free(p, st);
@@ -441,6 +453,9 @@ bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
         return BBC_OK;
     if (g->tile_items) dev_free(g->tile_items, st);
     if (g->warp_items) dev_free(g->warp_items, st);
+    if (g->wt_items) dev_free(g->wt_items, st);
+    g->wt_items = nullptr;
+    g->n_wt = 0;
     if (g->bnd) dev_free(g->bnd, st);
     if (g->boff) dev_free(g->boff, st);
     g->tile_items = nullptr;
@@ -457,26 +472,37 @@ bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
         return BBC_OK;
     }
     Scratch sc(st);
-    int32_t *nt = nullptr, *nh = nullptr;
-    int64_t *pt = nullptr, *ph = nullptr, *nb = nullptr;
+    int32_t *nt = nullptr, *nh = nullptr, *nw = nullptr;
+    int64_t *pt = nullptr, *ph = nullptr, *pw = nullptr, *nb = nullptr;
     BBC_TRY(sc.get(&nt, (size_t)nS));
     BBC_TRY(sc.get(&nh, (size_t)nS));
+    BBC_TRY(sc.get(&nw, (size_t)nS));
     BBC_TRY(sc.get(&pt, (size_t)nS + 1));
     BBC_TRY(sc.get(&ph, (size_t)nS + 1));
+    BBC_TRY(sc.get(&pw, (size_t)nS + 1));
     BBC_TRY(sc.get(&nb, (size_t)nS));
     BBC_TRY(dev_alloc_n(&g->boff, (size_t)nS + 1, st));
-    ClassifyParams P{g->nS, g->orient_low, t.tile_words, t.warp_max_wedges, t.split_wedges};
+    ClassifyParams P{g->nS, g->orient_low, t.tile_words, t.warp_max_wedges, t.split_wedges,
+                     t.plain ? 0 : 1};
     note_launch();
-    k_classify<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, nt, nh, nb);
+    k_classify<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, nt, nh, nb, nw);
     BBC_LAUNCH_CHECK("k_classify");
     BBC_TRY(exclusive_scan_i32_to_i64(nt, pt, nS, st));
     BBC_TRY(exclusive_scan_i32_to_i64(nh, ph, nS, st));
+    BBC_TRY(exclusive_scan_i32_to_i64(nw, pw, nS, st));
     BBC_TRY(exclusive_scan_i64(nb, g->boff, nS, st));
-    int64_t counts[3];
+    int64_t counts[4];
     BBC_CUDA_TRY(cudaMemcpyAsync(&counts[0], pt + nS, 8, cudaMemcpyDeviceToHost, st));
     BBC_CUDA_TRY(cudaMemcpyAsync(&counts[1], ph + nS, 8, cudaMemcpyDeviceToHost, st));
     BBC_CUDA_TRY(cudaMemcpyAsync(&counts[2], g->boff + nS, 8, cudaMemcpyDeviceToHost, st));
+    BBC_CUDA_TRY(cudaMemcpyAsync(&counts[3], pw + nS, 8, cudaMemcpyDeviceToHost, st));
     BBC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (counts[3] > INT32_MAX) {
+        set_error("work list longer than 2^31 items");
+        return BBC_E_INVALID_ARG;
+    }
+    BBC_TRY(dev_alloc_n(&g->wt_items, (size_t)counts[3], st));
+    g->n_wt = (int32_t)counts[3];
     BBC_TRY(dev_alloc_n(&g->bnd, (size_t)counts[2], st));
     if (counts[2] > 0 && g->n_edges > 0) {
         note_launch();
@@ -498,8 +524,8 @@ bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
     BBC_TRY(dev_alloc_n(&g->tile_items, (size_t)ntile, st));
     g->n_tile = (int32_t)ntile;
     note_launch();
-    k_emit_items<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, pt, ph, raw, keys,
-                                                     g->warp_items);
+    k_emit_items<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, pt, ph, pw, raw, keys,
+                                                     g->warp_items, g->wt_items);
     BBC_LAUNCH_CHECK("k_emit_items");
     // Order the tile items by expected cost, largest first (the plain schedule keeps
     // rank order).

@@ -41,7 +41,7 @@ struct Request {
     std::vector<int8_t> s;
     size_t reserve = 0;          // device bytes reserved at admission
     bbc_graph *g = nullptr;
-    int32_t tile_done = 0, warp_done = 0;
+    int32_t tile_done = 0, warp_done = 0, wt_done = 0;
     bool done = false;
     bbc_status status = BBC_OK;
     uint64_t balanced = 0;
@@ -93,6 +93,8 @@ struct bbc_server {
     size_t tiles_cap = 0;
     bbc::HashItem *warps = nullptr;
     size_t warps_cap = 0;
+    bbc::HashItem *wts = nullptr;
+    size_t wts_cap = 0;
     bbc::CopyJob *djobs = nullptr;
     size_t djobs_cap = 0;
     bbc::QueueState *queue_state = nullptr;
@@ -182,27 +184,33 @@ bbc_status run_tick(bbc_server *S, std::vector<Request *> &act) {
     const int chunk = 4 * device_sm_count() * S->tuning.blocks_per_sm;
     const size_t n = act.size();
     std::vector<DevGraph> hd(n);
-    std::vector<CopyJob> jt, jh;
-    int64_t nt = 0, nh = 0;
-    std::vector<int32_t> take_t(n), take_h(n);
+    std::vector<CopyJob> jt, jh, jw;
+    int64_t nt = 0, nh = 0, nw = 0;
+    std::vector<int32_t> take_t(n), take_h(n), take_w(n);
     for (size_t i = 0; i < n; ++i) {
         bbc_graph *g = act[i]->g;
         hd[i] = host_descriptor(g, false, true);
         const int32_t rt = g->n_tile - act[i]->tile_done;
         const int32_t rh = g->n_warp - act[i]->warp_done;
+        const int32_t rw = g->n_wt - act[i]->wt_done;
         take_t[i] = std::min(rt, chunk);
         take_h[i] = std::min(rh, 64 * chunk);
+        take_w[i] = std::min(rw, 16 * chunk);
         if (take_t[i] > 0)
             jt.push_back(CopyJob{g->tile_items + act[i]->tile_done, nt, take_t[i], (int32_t)i});
         if (take_h[i] > 0)
             jh.push_back(CopyJob{g->warp_items + act[i]->warp_done, nh, take_h[i], (int32_t)i});
+        if (take_w[i] > 0)
+            jw.push_back(CopyJob{g->wt_items + act[i]->wt_done, nw, take_w[i], (int32_t)i});
         nt += take_t[i];
         nh += take_h[i];
+        nw += take_w[i];
     }
     BBC_TRY(ensure(&S->dgraphs, &S->dgraphs_cap, n, st));
     BBC_TRY(ensure(&S->tiles, &S->tiles_cap, (size_t)std::max<int64_t>(nt, 1), st));
     BBC_TRY(ensure(&S->warps, &S->warps_cap, (size_t)std::max<int64_t>(nh, 1), st));
-    BBC_TRY(ensure(&S->djobs, &S->djobs_cap, std::max(jt.size(), jh.size()) + 1, st));
+    BBC_TRY(ensure(&S->wts, &S->wts_cap, (size_t)std::max<int64_t>(nw, 1), st));
+    BBC_TRY(ensure(&S->djobs, &S->djobs_cap, std::max(jt.size(), std::max(jh.size(), jw.size())) + 1, st));
     if (!S->queue_state) BBC_TRY(dev_alloc_n(&S->queue_state, 1, st));
     if (S->host_totals_cap < 2 * n) {
         if (S->host_totals) cudaFreeHost(S->host_totals);
@@ -213,6 +221,7 @@ bbc_status run_tick(bbc_server *S, std::vector<Request *> &act) {
     BBC_CUDA_TRY(cudaMemcpyAsync(S->dgraphs, hd.data(), sizeof(DevGraph) * n, cudaMemcpyHostToDevice, st));
     BBC_TRY(concat_items(jt, true, S->tiles, S->djobs, st));
     BBC_TRY(concat_items(jh, false, S->warps, S->djobs, st));
+    BBC_TRY(concat_items(jw, false, S->wts, S->djobs, st));
     BBC_CUDA_TRY(cudaMemsetAsync(S->queue_state, 0, sizeof(QueueState), st));
     CountLaunch L{};
     L.graphs = S->dgraphs;
@@ -220,12 +229,15 @@ bbc_status run_tick(bbc_server *S, std::vector<Request *> &act) {
     L.n_tile_items = (int32_t)nt;
     L.warp_items = S->warps;
     L.n_warp_items = (int32_t)nh;
+    L.wt_items = S->wts;
+    L.n_wt_items = (int32_t)nw;
     L.queue = S->queue_state;
     L.tuning = S->tuning;
     BBC_TRY(launch_count(L, st));
     for (size_t i = 0; i < n; ++i) {
         act[i]->tile_done += take_t[i];
         act[i]->warp_done += take_h[i];
+        act[i]->wt_done += take_w[i];
         BBC_CUDA_TRY(cudaMemcpyAsync(S->host_totals + 2 * i, act[i]->g->totals, 16,
                                      cudaMemcpyDeviceToHost, st));
     }
@@ -257,7 +269,8 @@ void worker_main(bbc_server *S) {
         std::vector<Request *> still;
         for (size_t i = 0; i < act.size(); ++i) {
             Request *r = act[i];
-            const bool complete = r->tile_done >= r->g->n_tile && r->warp_done >= r->g->n_warp;
+            const bool complete = r->tile_done >= r->g->n_tile && r->warp_done >= r->g->n_warp &&
+                                  r->wt_done >= r->g->n_wt;
             if (st != BBC_OK || complete) {
                 release_graph(r->g, S->stream);
                 r->g = nullptr;
@@ -432,7 +445,7 @@ void bbc_server_destroy(bbc_server *S) {
         r->g = nullptr;
         if (!r->done) finish_locked(S, r, BBC_E_CANCELLED, 0);
     }
-    void *bufs[] = {S->dgraphs, S->tiles, S->warps, S->djobs, S->queue_state};
+    void *bufs[] = {S->dgraphs, S->tiles, S->warps, S->wts, S->djobs, S->queue_state};
     for (void *p : bufs)
         if (p) dev_free(p, S->stream);
     cudaStreamSynchronize(S->stream);
