@@ -226,7 +226,8 @@ void bbc_server_destroy(bbc_server *s);
  * Accounting for reports (not part of the counting): bbc_launch_count is the number of
  * CUDA kernels this library has launched in this process. Between bbc_profile_start and
  * bbc_profile_stop every launch of a counting kernel (outside stream capture) is
- * bracketed by CUDA events on its own stream; bbc_profile_stop waits for them and fills
+ * bracketed by CUDA events on its own stream, and bbc_count_batch launches its recorded
+ * work directly instead of replaying the CUDA graph; bbc_profile_stop waits for them and fills
  * up to `capacity` entries, one per kernel, with its launches and summed device time
  * (*count receives the number of kernels seen).
  */

@@ -89,10 +89,12 @@ struct ProfSlot {
     bool used = false;
 };
 std::vector<ProfSlot> g_prof;
-const char *const kProfNames[kProfKinds] = {"k_tile", "k_warp_hash", "k_warp_tile"};
+const char *const kProfNames[kProfKinds] = {"k_tile", "k_warp_hash", "k_warp_tile", "k_group_tile"};
 }  // namespace
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+bool profiling_active() { return g_prof_on.load(std::memory_order_relaxed); }
 
 int profile_begin(int kind, cudaStream_t st) {
     if (!g_prof_on.load(std::memory_order_relaxed)) return -1;
@@ -216,6 +218,8 @@ bbc_status count_graph(bbc_graph *g, uint64_t *totals_dev, uint64_t *per_u, uint
     L.n_warp_items = g->n_warp;
     L.wt_items = g->wt_items;
     L.n_wt_items = g->n_wt;
+    L.gt_items = g->gt_items;
+    L.n_gt_items = g->n_gt;
     L.queue = g->queue;
     L.tuning = T;
     BBC_TRY(launch_count(L, st));

@@ -2,8 +2,8 @@
 // persistent launch over a device-side (graph, anchor, tile range) work list.
 //
 // A "plan" concatenates the member graphs' work items (tagging each with its graph
-// index), re-orders all tile items by expected wedge count across graphs (largest
-// first), and records the memsets and counting launches into a CUDA graph once. Later
+// index) graph by graph, heaviest graph first, and records the memsets and counting
+// launches into a CUDA graph once. Later
 // calls with the same graphs and tuning replay that graph: one launch of the whole
 // counting step, whatever the number of graphs.
 #include <algorithm>
@@ -33,34 +33,6 @@ __global__ void k_concat_items(const CopyJob *__restrict__ jobs, Item *__restric
     }
 }
 
-// 16-bit key ordering tile items by expected wedges, largest first, across graphs.
-__global__ void k_tile_item_keys(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items,
-                                 int64_t n, int tile_words, uint32_t *__restrict__ keys,
-                                 uint32_t *__restrict__ order) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const TileItem it = items[i];
-        const DevGraph &G = graphs[it.graph];
-        const int cw = tile_width_of(it);
-        const long long ept = cw == 0 ? 2ll * tile_words : (cw == 1 ? tile_words : tile_words / 2);
-        const long long span = G.orient_low ? it.anchor : (long long)G.nS - 1 - it.anchor;
-        const long long nt = (span + ept - 1) / ept;
-        const double cost = (double)G.wl[it.anchor] * (double)(tile_end_of(it) - it.tile_begin) /
-                                (double)(nt > 0 ? nt : 1) + 1.0;
-        int q = (int)(log2(cost) * 1024.0);
-        q = q < 0 ? 0 : (q > 65535 ? 65535 : q);
-        keys[i] = 65535u - (uint32_t)q;
-        order[i] = (uint32_t)i;
-    }
-}
-
-__global__ void k_gather_tile_items(const TileItem *__restrict__ in, const uint32_t *__restrict__ order,
-                                    int64_t n, TileItem *__restrict__ out) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = in[order[i]];
-}
-
 struct Plan {
     std::vector<uint64_t> uids;
     std::vector<uint64_t> versions;   // each graph's layout_version when the plan was built
@@ -74,14 +46,16 @@ struct Plan {
     TileItem *tiles = nullptr;
     HashItem *warp = nullptr;
     HashItem *wt = nullptr;
-    int32_t n_tile = 0, n_warp = 0, n_wt = 0;
+    HashItem *gt = nullptr;
+    int32_t n_tile = 0, n_warp = 0, n_wt = 0, n_gt = 0;
     cudaStream_t stream = nullptr;            // capture / replay stream
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t exec = nullptr;
+    CountLaunch launch{};                     // what the graph records (for profiled runs)
 
     ~Plan() {
         if (exec) cudaGraphExecDestroy(exec);
-        void *ps[] = {dgraphs, totals, queue, tiles, warp, wt};
+        void *ps[] = {dgraphs, totals, queue, tiles, warp, wt, gt};
         for (void *p : ps)
             if (p) dev_free(p, stream);
         if (stream) cudaStreamSynchronize(stream);
@@ -149,43 +123,55 @@ bbc_status build_plan(int32_t n, bbc_graph *const *gs, const Tuning &T, std::uni
         P->versions.push_back(gs[i]->layout_version);
     }
     std::vector<DevGraph> hd(n);
-    std::vector<CopyJob> jt, jh, jw;
-    int64_t nt = 0, nh = 0, nw = 0;
+    std::vector<CopyJob> jt, jh, jw, jg;
+    int64_t nt = 0, nh = 0, nw = 0, ngr = 0;
     BBC_TRY(dev_alloc_n(&P->totals, (size_t)2 * n, st));
     for (int i = 0; i < n; ++i) {
-        bbc_graph *g = gs[i];
-        hd[i] = host_descriptor(g, false, true);
+        hd[i] = host_descriptor(gs[i], false, true);
         hd[i].totals = P->totals + 2 * i;
+    }
+    // Graph-major queues, heaviest graph first: a graph's items stay together, so only a
+    // few graphs' rows are being read at any time and they stay in L2.
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return gs[x]->wedges > gs[y]->wedges; });
+    for (int i : order) {
+        bbc_graph *g = gs[i];
         if (g->n_tile) jt.push_back(CopyJob{g->tile_items, nt, g->n_tile, i});
         if (g->n_warp) jh.push_back(CopyJob{g->warp_items, nh, g->n_warp, i});
         if (g->n_wt) jw.push_back(CopyJob{g->wt_items, nw, g->n_wt, i});
+        if (g->n_gt) jg.push_back(CopyJob{g->gt_items, ngr, g->n_gt, i});
         nt += g->n_tile;
         nh += g->n_warp;
         nw += g->n_wt;
+        ngr += g->n_gt;
     }
-    if (nt > INT32_MAX || nh > INT32_MAX || nw > INT32_MAX) {
+    if (nt > INT32_MAX || nh > INT32_MAX || nw > INT32_MAX || ngr > INT32_MAX) {
         set_error("bbc_count_batch: too many work items");
         return BBC_E_INVALID_ARG;
     }
     P->n_tile = (int32_t)nt;
     P->n_warp = (int32_t)nh;
     P->n_wt = (int32_t)nw;
+    P->n_gt = (int32_t)ngr;
     BBC_TRY(dev_alloc_n(&P->dgraphs, (size_t)n, st));
     BBC_TRY(dev_alloc_n(&P->queue, 1, st));
     BBC_TRY(dev_alloc_n(&P->tiles, (size_t)nt, st));
     BBC_TRY(dev_alloc_n(&P->warp, (size_t)nh, st));
     BBC_TRY(dev_alloc_n(&P->wt, (size_t)nw, st));
+    BBC_TRY(dev_alloc_n(&P->gt, (size_t)ngr, st));
     BBC_CUDA_TRY(cudaMallocHost(&P->host_totals, sizeof(unsigned long long) * 2 * (size_t)std::max(n, 1)));
     BBC_CUDA_TRY(cudaMemcpyAsync(P->dgraphs, hd.data(), sizeof(DevGraph) * (size_t)n,
                                  cudaMemcpyHostToDevice, st));
     // concatenate, tagging each item with its graph index
     CopyJob *djobs = nullptr;
-    const size_t maxj = std::max(jt.size(), std::max(jh.size(), jw.size()));
+    const size_t maxj = std::max(std::max(jt.size(), jg.size()), std::max(jh.size(), jw.size()));
     BBC_TRY(dev_alloc_n(&djobs, maxj, st));
     struct Part {
         std::vector<CopyJob> *jobs;
         int which;
-    } parts[3] = {{&jt, 0}, {&jh, 2}, {&jw, 3}};
+    } parts[4] = {{&jt, 0}, {&jh, 2}, {&jw, 3}, {&jg, 4}};
     bbc_status s = BBC_OK;
     for (auto &pt : parts) {
         if (pt.jobs->empty()) continue;
@@ -200,6 +186,7 @@ bbc_status build_plan(int32_t n, bbc_graph *const *gs, const Tuning &T, std::uni
         if (pt.which == 0) k_concat_items<TileItem><<<nb, kThreads, 0, st>>>(djobs, P->tiles);
         if (pt.which == 2) k_concat_items<HashItem><<<nb, kThreads, 0, st>>>(djobs, P->warp);
         if (pt.which == 3) k_concat_items<HashItem><<<nb, kThreads, 0, st>>>(djobs, P->wt);
+        if (pt.which == 4) k_concat_items<HashItem><<<nb, kThreads, 0, st>>>(djobs, P->gt);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // djobs is reused
         if (e != cudaSuccess) {
@@ -209,28 +196,6 @@ bbc_status build_plan(int32_t n, bbc_graph *const *gs, const Tuning &T, std::uni
     }
     dev_free(djobs, st);
     BBC_TRY(s);
-    // order tile items across graphs, heaviest first
-    if (nt > 1) {
-        const int64_t cnt = nt;
-        TileItem *items = P->tiles;
-        uint32_t *keys = nullptr, *order = nullptr;
-        TileItem *sorted = nullptr;
-        BBC_TRY(dev_alloc_n(&keys, (size_t)cnt, st));
-        BBC_TRY(dev_alloc_n(&order, (size_t)cnt, st));
-        BBC_TRY(dev_alloc_n(&sorted, (size_t)cnt, st));
-        const unsigned grid = (unsigned)std::min<int64_t>((cnt + kThreads - 1) / kThreads, 4096);
-        note_launch();
-        k_tile_item_keys<<<grid, kThreads, 0, st>>>(P->dgraphs, items, cnt, T.tile_words, keys, order);
-        BBC_LAUNCH_OK("k_tile_item_keys");
-        BBC_TRY(radix_sort_pairs(keys, order, cnt, 16, st));
-        note_launch();
-        k_gather_tile_items<<<grid, kThreads, 0, st>>>(items, order, cnt, sorted);
-        BBC_LAUNCH_OK("k_gather_tile_items");
-        dev_free(keys, st);
-        dev_free(order, st);
-        dev_free(items, st);
-        P->tiles = sorted;
-    }
     BBC_CUDA_TRY(cudaStreamSynchronize(st));
     // record the counting step once
     BBC_TRY(configure_count_kernels());
@@ -242,8 +207,11 @@ bbc_status build_plan(int32_t n, bbc_graph *const *gs, const Tuning &T, std::uni
     L.n_warp_items = P->n_warp;
     L.wt_items = P->wt;
     L.n_wt_items = P->n_wt;
+    L.gt_items = P->gt;
+    L.n_gt_items = P->n_gt;
     L.queue = P->queue;
     L.tuning = T;
+    P->launch = L;
     BBC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     cudaMemsetAsync(P->totals, 0, sizeof(unsigned long long) * 2 * (size_t)n, st);
     cudaMemsetAsync(P->queue, 0, sizeof(QueueState), st);
@@ -298,7 +266,18 @@ bbc_status run_plan(Plan *p, uint64_t *balanced, cudaStream_t st, float *ms) {
         BBC_CUDA_TRY(cudaEventCreate(&t1));
         BBC_CUDA_TRY(cudaEventRecord(t0, p->stream));
     }
-    BBC_CUDA_TRY(cudaGraphLaunch(p->exec, p->stream));
+    if (profiling_active()) {
+        // the same work launched directly, so that the kernels' event brackets apply
+        BBC_CUDA_TRY(cudaMemsetAsync(p->totals, 0, sizeof(unsigned long long) * 2 * (size_t)p->n,
+                                     p->stream));
+        BBC_CUDA_TRY(cudaMemsetAsync(p->queue, 0, sizeof(QueueState), p->stream));
+        BBC_TRY(launch_count(p->launch, p->stream));
+        BBC_CUDA_TRY(cudaMemcpyAsync(p->host_totals, p->totals,
+                                     sizeof(unsigned long long) * 2 * (size_t)p->n,
+                                     cudaMemcpyDeviceToHost, p->stream));
+    } else {
+        BBC_CUDA_TRY(cudaGraphLaunch(p->exec, p->stream));
+    }
     if (ms) BBC_CUDA_TRY(cudaEventRecord(t1, p->stream));
     BBC_CUDA_TRY(cudaEventRecord(p->ev_out, p->stream));
     BBC_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_out, 0));

@@ -66,11 +66,13 @@ struct HashItem {
     int32_t cw;
 };
 
-// Words of one warp's counter table in the warp-tile kernel, and the endpoints it holds
-// per counter width code.
+// Words of one warp's counter table in the group-tile kernel (a group of gw warps pools
+// gw tables), and the endpoints such a table holds per counter width code.
 constexpr int kWtWords = 1536;
-__host__ __device__ constexpr uint32_t warp_tile_endpoints(int cw) {
-    return cw == 0 ? 2u * kWtWords : (cw == 1 ? (uint32_t)kWtWords : (uint32_t)kWtWords / 2u);
+constexpr int kGroupWarps = 4;
+__host__ __device__ constexpr uint32_t group_tile_endpoints(int gw, int cw) {
+    return cw == 0 ? 2u * kWtWords * gw
+                   : (cw == 1 ? (uint32_t)kWtWords * gw : (uint32_t)kWtWords * gw / 2u);
 }
 
 // Queue heads and the error word of the persistent kernels; zeroed before a launch.
@@ -80,6 +82,7 @@ struct QueueState {
     unsigned int spare;
     unsigned int error;        // nonzero: a kernel saw an impossible state (see kErr*)
     unsigned int wt_head;      // warp-tile items
+    unsigned int gt_head;      // group-tile items
 };
 
 enum : unsigned int {
@@ -123,8 +126,9 @@ void note_launch();
 // Optional per-kernel timing (bbc_profile_start / bbc_profile_stop): while enabled, the
 // counting kernels are bracketed by CUDA events on their own stream. profile_begin
 // returns a token (-1 when profiling is off or the stream is being captured).
-enum { kProfTile = 0, kProfHash = 1, kProfWarpTile = 2, kProfKinds = 3 };
+enum { kProfTile = 0, kProfHash = 1, kProfWarpTile = 2, kProfGroupTile = 3, kProfKinds = 4 };
 int profile_begin(int kind, cudaStream_t st);
+bool profiling_active();
 void profile_end(int token, cudaStream_t st);
 
 // ----------------------------------------------------------------------------- memory
@@ -163,6 +167,8 @@ struct CountLaunch {
     int32_t n_warp_items;
     const HashItem *wt_items;   // device, warp-tile items
     int32_t n_wt_items;
+    const HashItem *gt_items;   // device, group-tile items
+    int32_t n_gt_items;
     QueueState *queue;          // device, zeroed by the caller before the launch
     Tuning tuning;
 };

@@ -24,6 +24,7 @@
 // counters: the pair {a, w} adds f = C(p,2) + C(n,2) to both b(a) and b(w); and a wedge
 // a - c - w of type t lies in (count_t(a, w) - 1) balanced butterflies through c, so a
 // second sweep over the same slices, after the counters are complete, adds that to b(c).
+#include <algorithm>
 #include <type_traits>
 
 #include "graph.cuh"
@@ -114,13 +115,23 @@ struct HashCounter {
 
 // ----------------------------------------------------------------------------- sweep
 
+// Per-warp staging of one batch of 32 centres' short slices (the warp sweep's table).
+struct WarpStage {
+    uint32_t start[32];
+    uint32_t excl[33];
+    uint32_t sg[32];
+};
+
 // One warp's pass over all oriented wedges of anchor rows [sb, se) (the warp kernels'
 // sweep: their anchors fit one counter table). MODE 0 bumps the counters; MODE 1 (the
 // per-vertex centre pass) reads them and adds (count - 1) per wedge to the centre's b.
-// The warp takes batches of 32 centres from *batch_ctr; lane j owns centre j's slice.
+// Warps take batches of 32 centres from *batch_ctr; lane j owns centre j's slice. Long
+// slices are swept by the whole warp with 16-byte loads; short ones are concatenated in
+// the warp's stage and cut into contiguous per-lane shares.
 template <int MODE, class Counter>
 __device__ __forceinline__ void warp_sweep(const DevGraph &G, int64_t sb, int64_t se,
-                                      const Counter &ctr, int *batch_ctr, uint32_t *sacc) {
+                                      const Counter &ctr, int *batch_ctr, uint32_t *sacc,
+                                      WarpStage &ws) {
     const int lane = threadIdx.x & 31;
     const int64_t nbatch = (se - sb + 31) >> 5;
     const uint32_t *__restrict__ rowC = G.rowC;
@@ -130,9 +141,7 @@ __device__ __forceinline__ void warp_sweep(const DevGraph &G, int64_t sb, int64_
         bi = __shfl_sync(kFull, bi, 0);
         if (bi >= nbatch) break;
         const int64_t ci = sb + (int64_t)bi * 32 + lane;
-        long long b = 0;
-        int len = 0;
-        uint32_t sg = 0, c = 0;
+        uint32_t b = 0, len = 0, sg = 0, c = 0;
         if (ci < se) {
             // the whole endpoint range of the anchor inside row c (known from preparation)
             const uint32_t ent = __ldg(G.rowS + ci);
@@ -140,66 +149,112 @@ __device__ __forceinline__ void warp_sweep(const DevGraph &G, int64_t sb, int64_
             sg = ent & kSignBit;
             const uint2 r = __ldg(G.rng + ci);
             b = r.x;
-            len = (int)(r.y - r.x);
+            len = r.y - r.x;
         }
-        // Long slices: the whole warp sweeps one slice at a time, coalesced.
-        unsigned longm = __ballot_sync(kFull, len >= kLongSlice);
+        // Long slices: the whole warp sweeps one slice at a time, coalesced 16-byte loads.
+        unsigned longm = __ballot_sync(kFull, len >= (uint32_t)kLongSlice);
         while (longm) {
             const int j = __ffs(longm) - 1;
             longm &= longm - 1;
-            const long long bj = __shfl_sync(kFull, b, j);
-            const int lj = __shfl_sync(kFull, len, j);
+            const uint32_t s = __shfl_sync(kFull, b, j);
+            const uint32_t n = __shfl_sync(kFull, len, j);
             const uint32_t sj = __shfl_sync(kFull, sg, j);
             unsigned long long acc = 0;
-            for (int k = lane; k < lj; k += 32) {
-                const uint32_t x = __ldg(rowC + bj + k);
-                const uint32_t t = (x ^ sj) >> 31;
+            auto visit = [&](uint32_t x) {
                 if (MODE == 0)
-                    ctr.bump(x & kIdMask, t);
+                    ctr.bump(x & kIdMask, (x ^ sj) >> 31);
                 else
-                    acc += ctr.peek(x & kIdMask, t) - 1u;
+                    acc += ctr.peek(x & kIdMask, (x ^ sj) >> 31) - 1u;
+            };
+            const uint32_t head = min(n, (4u - (s & 3u)) & 3u);
+            if ((uint32_t)lane < head) visit(__ldg(rowC + s + lane));
+            const uint32_t m4 = (n - head) >> 2;
+            const uint4 *v4 = reinterpret_cast<const uint4 *>(rowC + s + head);
+            for (uint32_t q = lane; q < m4; q += 64) {
+                const uint4 xa = __ldg(v4 + q);
+                const bool has_b = q + 32 < m4;
+                uint4 xb = make_uint4(0u, 0u, 0u, 0u);
+                if (has_b) xb = __ldg(v4 + q + 32);
+                visit(xa.x);
+                visit(xa.y);
+                visit(xa.z);
+                visit(xa.w);
+                if (has_b) {
+                    visit(xb.x);
+                    visit(xb.y);
+                    visit(xb.z);
+                    visit(xb.w);
+                }
             }
+            const uint32_t rest = (n - head) & 3u;
+            if ((uint32_t)lane < rest) visit(__ldg(rowC + s + head + 4 * m4 + lane));
             if (MODE == 1) {
                 acc = warp_sum(acc);
                 if (lane == j && acc) atomicAdd(G.bC + c, acc);
             }
         }
-        // Short slices: flattened so that every lane has a wedge each step.
-        const int sl = len < kLongSlice ? len : 0;
-        int incl = sl;
+        // Short slices: staged, then contiguous equal shares per lane.
+        const uint32_t sl = len < (uint32_t)kLongSlice ? len : 0u;
+        uint32_t incl = sl;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(kFull, incl, o);
+            const uint32_t y = __shfl_up_sync(kFull, incl, o);
             if (lane >= o) incl += y;
         }
-        const int total = __shfl_sync(kFull, incl, 31);
-        const int excl = incl - sl;
-        if (MODE == 1) {
-            sacc[lane] = 0;
-            __syncwarp();
-        }
-        for (int base = 0; base < total; base += 32) {
-            const int k = base + lane;
-            int j = 0;  // number of lanes whose inclusive end is <= k
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        ws.start[lane] = b;
+        ws.excl[lane] = incl - sl;
+        ws.sg[lane] = sg;
+        if (lane == 31) ws.excl[32] = total;
+        if (MODE == 1) sacc[lane] = 0;
+        __syncwarp();
+        uint32_t k = (uint32_t)(((unsigned long long)total * lane) >> 5);
+        const uint32_t k1 = (uint32_t)(((unsigned long long)total * (lane + 1)) >> 5);
+        if (k < k1) {
+            int j = 0;  // last staged slice whose start offset is <= k
 #pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int vv = __shfl_sync(kFull, incl, j + step - 1);
-                if (vv <= k) j += step;
-            }
-            const long long bj = __shfl_sync(kFull, b, j);
-            const int ej = __shfl_sync(kFull, excl, j);
-            const uint32_t sj = __shfl_sync(kFull, sg, j);
-            if (k < total) {
-                const uint32_t x = __ldg(rowC + bj + (k - ej));
-                const uint32_t t = (x ^ sj) >> 31;
+            for (int step = 16; step > 0; step >>= 1)
+                if (ws.excl[j + step] <= k) j += step;
+            uint32_t nb = ws.excl[j + 1];
+            uint32_t base = ws.start[j] - ws.excl[j];
+            uint32_t sgj = ws.sg[j];
+            uint32_t acc = 0;
+            uint32_t x = __ldg(rowC + (uint32_t)(base + k));
+            for (;;) {
+                const uint32_t k2 = k + 1;
+                int j2 = j;
+                uint32_t nb2 = nb, base2 = base, sg2 = sgj, x2 = 0;
+                if (k2 < k1) {
+                    if (k2 >= nb2) {
+                        do {
+                            ++j2;
+                            nb2 = ws.excl[j2 + 1];
+                        } while (nb2 <= k2);
+                        base2 = ws.start[j2] - ws.excl[j2];
+                        sg2 = ws.sg[j2];
+                    }
+                    x2 = __ldg(rowC + (uint32_t)(base2 + k2));
+                }
                 if (MODE == 0)
-                    ctr.bump(x & kIdMask, t);
+                    ctr.bump(x & kIdMask, (x ^ sgj) >> 31);
                 else
-                    atomicAdd(sacc + j, ctr.peek(x & kIdMask, t) - 1u);
+                    acc += ctr.peek(x & kIdMask, (x ^ sgj) >> 31) - 1u;
+                if (k2 >= k1) break;
+                if (MODE == 1 && j2 != j && acc) {
+                    atomicAdd(sacc + j, acc);
+                    acc = 0;
+                }
+                k = k2;
+                j = j2;
+                nb = nb2;
+                base = base2;
+                sgj = sg2;
+                x = x2;
             }
+            if (MODE == 1 && acc) atomicAdd(sacc + j, acc);
         }
+        __syncwarp();
         if (MODE == 1) {
-            __syncwarp();
             if (sl > 0 && sacc[lane]) atomicAdd(G.bC + c, (unsigned long long)sacc[lane]);
             __syncwarp();
         }
@@ -674,6 +729,7 @@ k_warp_hash(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ it
     extern __shared__ uint4 smem_hash[];
     __shared__ uint32_t s_acc[kHashWarps][32];
     __shared__ int s_batch[kHashWarps];
+    __shared__ WarpStage s_stage[kHashWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *keys = reinterpret_cast<uint32_t *>(smem_hash) + warp * 2 * kHashSlots;
     uint32_t *vals = keys + kHashSlots;
@@ -697,12 +753,12 @@ k_warp_hash(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ it
         const HashCounter ctr{keys, vals, (1u << lg) - 1u, 32 - lg, &q->error};
         if (lane == 0) s_batch[warp] = 0;
         __syncwarp();
-        warp_sweep<0>(G, sb, se, ctr, &s_batch[warp], nullptr);
+        warp_sweep<0>(G, sb, se, ctr, &s_batch[warp], nullptr, s_stage[warp]);
         __syncwarp();
         if (G.bC) {
             if (lane == 0) s_batch[warp] = 0;
             __syncwarp();
-            warp_sweep<1>(G, sb, se, ctr, &s_batch[warp], s_acc[warp]);
+            warp_sweep<1>(G, sb, se, ctr, &s_batch[warp], s_acc[warp], s_stage[warp]);
             __syncwarp();
         }
         unsigned long long bal = 0, unb = 0;
@@ -730,33 +786,44 @@ k_warp_hash(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ it
 }
 
 
-// ----------------------------------------------------------------------------- warp tiles
+// ----------------------------------------------------------------------------- group tiles
 
-// One warp's dense counter table for an anchor whose whole endpoint range fits it
-// (single-tile anchors of small graphs): no block barrier, sixteen anchors in flight per
-// block.
-template <int CW>
-__device__ void warp_tile_item(const DevGraph &G, int a, uint32_t *tile, int *batch_ctr,
-                               uint32_t *sacc) {
+// Barrier over the GW warps of one group (a named barrier per group; a warp sync for a
+// group of one warp).
+template <int GW>
+__device__ __forceinline__ void group_sync(int grp) {
+    if (GW == 1)
+        __syncwarp();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(GW * 32) : "memory");
+}
+
+// A group of GW warps with a dense counter table of GW * kWtWords words counts one anchor
+// whose whole endpoint range fits the table (single-tile anchors of small and mid-sized
+// graphs): the group's warps share its centre batches, and no block barrier is involved.
+template <int GW, int CW>
+__device__ void group_tile_item(const DevGraph &G, int a, uint32_t *tile, int grp, int *batch_ctr,
+                                uint32_t *sacc, WarpStage &ws) {
     const int lane = threadIdx.x & 31;
+    const int gt = threadIdx.x - grp * GW * 32;
     const int64_t sb = G.rowS_off[a], se = G.rowS_off[a + 1];
     const uint32_t lo = G.orient_low ? 0u : (uint32_t)a + 1u;
     const uint32_t hi = G.orient_low ? (uint32_t)a : (uint32_t)G.nS;
     const TileCounter<CW> ctr{tile, lo};
-    if (lane == 0) *batch_ctr = 0;
-    __syncwarp();
-    warp_sweep<0>(G, sb, se, ctr, batch_ctr, nullptr);
-    __syncwarp();
+    if (gt == 0) *batch_ctr = 0;
+    group_sync<GW>(grp);
+    warp_sweep<0>(G, sb, se, ctr, batch_ctr, nullptr, ws);
+    group_sync<GW>(grp);
     if (G.bC) {
-        if (lane == 0) *batch_ctr = 0;
-        __syncwarp();
-        warp_sweep<1>(G, sb, se, ctr, batch_ctr, sacc);
-        __syncwarp();
+        if (gt == 0) *batch_ctr = 0;
+        group_sync<GW>(grp);
+        warp_sweep<1>(G, sb, se, ctr, batch_ctr, sacc, ws);
+        group_sync<GW>(grp);
     }
     const uint32_t n = hi - lo;
     unsigned long long bal = 0, unb = 0;
     if (CW == 2) {
-        for (uint32_t i = lane; i < n; i += 32) {
+        for (uint32_t i = gt; i < n; i += GW * 32) {
             const uint32_t p = tile[2 * i], m = tile[2 * i + 1];
             if ((p | m) == 0) continue;
             tile[2 * i] = 0;
@@ -765,7 +832,7 @@ __device__ void warp_tile_item(const DevGraph &G, int a, uint32_t *tile, int *ba
         }
     } else {
         const uint32_t words = CW == 0 ? (n + 1) / 2 : n;
-        for (uint32_t i = lane; i < words; i += 32) {
+        for (uint32_t i = gt; i < words; i += GW * 32) {
             const uint32_t x = tile[i];
             if (x == 0) continue;
             tile[i] = 0;
@@ -784,30 +851,34 @@ __device__ void warp_tile_item(const DevGraph &G, int a, uint32_t *tile, int *ba
         if (unb) atomicAdd(G.totals + 1, unb);
         if (G.bS && bal) atomicAdd(G.bS + a, bal);
     }
-    __syncwarp();
+    group_sync<GW>(grp);
 }
 
+template <int GW>
 __global__ void __launch_bounds__(kWtThreads, 2)
-k_warp_tile(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ items, int n_items,
-            QueueState *q) {
+k_group_tile(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ items, int n_items,
+             unsigned *head) {
     extern __shared__ uint4 smem_wt[];
     __shared__ uint32_t s_acc[kWtWarps][32];
-    __shared__ int s_batch[kWtWarps];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *tile = reinterpret_cast<uint32_t *>(smem_wt) + warp * kWtWords;
-    for (int i = lane; i < kWtWords; i += 32) tile[i] = 0;
-    __syncwarp();
+    __shared__ int s_batch[kWtWarps / GW];
+    __shared__ int s_item[kWtWarps / GW];
+    __shared__ WarpStage s_stage[kWtWarps];
+    const int warp = threadIdx.x >> 5;
+    const int grp = warp / GW;
+    const int gt = threadIdx.x - grp * GW * 32;
+    uint32_t *tile = reinterpret_cast<uint32_t *>(smem_wt) + grp * (GW * kWtWords);
+    for (int i = gt; i < GW * kWtWords; i += GW * 32) tile[i] = 0;
     for (;;) {
-        int it = 0;
-        if (lane == 0) it = (int)atomicAdd(&q->wt_head, 1u);
-        it = __shfl_sync(kFull, it, 0);
+        if (gt == 0) s_item[grp] = (int)atomicAdd(head, 1u);
+        group_sync<GW>(grp);
+        const int it = s_item[grp];
         if (it >= n_items) break;
         const HashItem item = items[it];
         const DevGraph &G = graphs[item.graph];
         switch (item.cw) {
-            case 0: warp_tile_item<0>(G, item.anchor, tile, &s_batch[warp], s_acc[warp]); break;
-            case 1: warp_tile_item<1>(G, item.anchor, tile, &s_batch[warp], s_acc[warp]); break;
-            default: warp_tile_item<2>(G, item.anchor, tile, &s_batch[warp], s_acc[warp]); break;
+            case 0: group_tile_item<GW, 0>(G, item.anchor, tile, grp, &s_batch[grp], s_acc[warp], s_stage[warp]); break;
+            case 1: group_tile_item<GW, 1>(G, item.anchor, tile, grp, &s_batch[grp], s_acc[warp], s_stage[warp]); break;
+            default: group_tile_item<GW, 2>(G, item.anchor, tile, grp, &s_batch[grp], s_acc[warp], s_stage[warp]); break;
         }
     }
 }
@@ -831,7 +902,10 @@ bbc_status configure_count_kernels() {
                                           maxopt - (int)fa.sharedSizeBytes));
         BBC_CUDA_TRY(cudaFuncSetAttribute(k_warp_hash, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           kHashWarps * 2 * kHashSlots * 4));
-        BBC_CUDA_TRY(cudaFuncSetAttribute(k_warp_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        BBC_CUDA_TRY(cudaFuncSetAttribute(k_group_tile<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          kWtWarps * kWtWords * 4));
+        BBC_CUDA_TRY(cudaFuncSetAttribute(k_group_tile<kGroupWarps>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           kWtWarps * kWtWords * 4));
         configured_device = dev;
     }
@@ -845,25 +919,38 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
     if (L.n_tile_items > 0) {
         const int tok = profile_begin(kProfTile, st);
         note_launch();
-        // work-queue schedule: persistent blocks; plain schedule: one block per item
-        const int grid = T.plain ? L.n_tile_items : sms * T.blocks_per_sm;
+        // work-queue schedule: persistent blocks (no more than there are items); plain
+        // schedule: one block per item
+        const int grid = T.plain ? L.n_tile_items : std::min(L.n_tile_items, sms * T.blocks_per_sm);
         k_tile<<<grid, kTileThreads, (size_t)T.tile_words * 4, st>>>(
             L.graphs, L.tile_items, L.n_tile_items, &L.queue->tile_head, T.tile_words, T.plain);
+        BBC_CUDA_TRY(cudaGetLastError());
+        profile_end(tok, st);
+    }
+    if (L.n_gt_items > 0) {
+        const int tok = profile_begin(kProfGroupTile, st);
+        note_launch();
+        constexpr int groups = kWtWarps / kGroupWarps;
+        k_group_tile<kGroupWarps><<<std::min((L.n_gt_items + groups - 1) / groups, sms * 2), kWtThreads,
+                                    kWtWarps * kWtWords * 4, st>>>(
+            L.graphs, L.gt_items, L.n_gt_items, &L.queue->gt_head);
         BBC_CUDA_TRY(cudaGetLastError());
         profile_end(tok, st);
     }
     if (L.n_wt_items > 0) {
         const int tok = profile_begin(kProfWarpTile, st);
         note_launch();
-        k_warp_tile<<<sms * 2, kWtThreads, kWtWarps * kWtWords * 4, st>>>(
-            L.graphs, L.wt_items, L.n_wt_items, L.queue);
+        k_group_tile<1><<<std::min((L.n_wt_items + kWtWarps - 1) / kWtWarps, sms * 2), kWtThreads,
+                          kWtWarps * kWtWords * 4, st>>>(
+            L.graphs, L.wt_items, L.n_wt_items, &L.queue->wt_head);
         BBC_CUDA_TRY(cudaGetLastError());
         profile_end(tok, st);
     }
     if (L.n_warp_items > 0) {
         const int tok = profile_begin(kProfHash, st);
         note_launch();
-        k_warp_hash<<<sms * 3, kHashThreads, kHashWarps * 2 * kHashSlots * 4, st>>>(
+        k_warp_hash<<<std::min((L.n_warp_items + kHashWarps - 1) / kHashWarps, sms * 3), kHashThreads,
+                      kHashWarps * 2 * kHashSlots * 4, st>>>(
             L.graphs, L.warp_items, L.n_warp_items, L.queue);
         BBC_CUDA_TRY(cudaGetLastError());
         profile_end(tok, st);

@@ -38,6 +38,8 @@ struct bbc_graph {
     int32_t n_warp = 0;
     bbc::HashItem *wt_items = nullptr;
     int32_t n_wt = 0;
+    bbc::HashItem *gt_items = nullptr;
+    int32_t n_gt = 0;
 
     // count-time state
     bbc::DevGraph *dgraph = nullptr;       // device copy of the descriptor

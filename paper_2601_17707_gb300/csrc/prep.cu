@@ -233,8 +233,9 @@ struct ClassifyParams {
     int warp_tiles;            // single-tile anchors that fit a warp's table go to k_warp_tile
 };
 
-// Work of one anchor: kind 0 none, 1 warp-hash item, 2 tile items, 3 warp-tile item
-// (its whole endpoint range fits one warp's counter table); for tiles, the
+// Work of one anchor: kind 0 none, 1 warp-hash item, 2 tile items, 3 warp-tile item (its
+// whole endpoint range fits one warp's counter table), 4 group-tile item (it fits a group
+// of warps' pooled table); for tiles, the
 // counter width code (largest reachable count min(degree, wedges) <= 255 / 65535 / more),
 // the number of tiles over its endpoint range and how many items they are split into.
 __device__ __forceinline__ void classify_one(const ClassifyParams &P, unsigned long long wl,
@@ -261,8 +262,12 @@ __device__ __forceinline__ void classify_one(const ClassifyParams &P, unsigned l
     *cw = w;
     *ntiles = nt;
     *groups = (int)g;
-    if (P.warp_tiles && span <= (long long)warp_tile_endpoints(w)) {
+    if (P.warp_tiles && span <= (long long)group_tile_endpoints(1, w)) {
         *kind = 3;
+        *ntiles = 1;
+        *groups = 1;
+    } else if (P.warp_tiles && span <= (long long)group_tile_endpoints(kGroupWarps, w)) {
+        *kind = 4;
         *ntiles = 1;
         *groups = 1;
     }
@@ -271,7 +276,7 @@ __device__ __forceinline__ void classify_one(const ClassifyParams &P, unsigned l
 __global__ void k_classify(ClassifyParams P, const unsigned long long *__restrict__ wl,
                            const int64_t *__restrict__ rowS_off, int32_t *__restrict__ n_tile,
                            int32_t *__restrict__ n_warp, int64_t *__restrict__ n_bnd,
-                           int32_t *__restrict__ n_wt) {
+                           int32_t *__restrict__ n_wt, int32_t *__restrict__ n_gt) {
     for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < P.nS;
          a += (int64_t)gridDim.x * blockDim.x) {
         int kind, cw, nt, g;
@@ -280,6 +285,7 @@ __global__ void k_classify(ClassifyParams P, const unsigned long long *__restric
         n_tile[a] = kind == 2 ? g : 0;
         n_warp[a] = kind == 1 ? 1 : 0;
         n_wt[a] = kind == 3 ? 1 : 0;
+        n_gt[a] = kind == 4 ? 1 : 0;
         n_bnd[a] = kind == 2 && nt > 1 ? deg * (nt - 1) : 0;
     }
 }
@@ -332,8 +338,9 @@ __global__ void k_tile_bounds(ClassifyParams P, const unsigned long long *__rest
 __global__ void k_emit_items(ClassifyParams P, const unsigned long long *__restrict__ wl,
                              const int64_t *__restrict__ rowS_off, const int64_t *__restrict__ pos_tile,
                              const int64_t *__restrict__ pos_warp, const int64_t *__restrict__ pos_wt,
-                             TileItem *__restrict__ tiles, uint32_t *__restrict__ keys,
-                             HashItem *__restrict__ warp, HashItem *__restrict__ wt) {
+                             const int64_t *__restrict__ pos_gt, TileItem *__restrict__ tiles,
+                             uint32_t *__restrict__ keys, HashItem *__restrict__ warp,
+                             HashItem *__restrict__ wt, HashItem *__restrict__ gt) {
     for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < P.nS;
          a += (int64_t)gridDim.x * blockDim.x) {
         int kind, cw, nt, g;
@@ -341,8 +348,12 @@ __global__ void k_emit_items(ClassifyParams P, const unsigned long long *__restr
         classify_one(P, w, rowS_off[a + 1] - rowS_off[a], (int)a, &kind, &cw, &nt, &g);
         if (kind == 1) {
             warp[pos_warp[a]] = HashItem{0, (int32_t)a, (int32_t)w, 0};
-        } else if (kind == 3) {
-            wt[pos_wt[a]] = HashItem{0, (int32_t)a, (int32_t)(w > 0x7fffffffull ? 0x7fffffff : w), cw};
+        } else if (kind == 3 || kind == 4) {
+            const HashItem h{0, (int32_t)a, (int32_t)(w > 0x7fffffffull ? 0x7fffffff : w), cw};
+            if (kind == 3)
+                wt[pos_wt[a]] = h;
+            else
+                gt[pos_gt[a]] = h;
         } else if (kind == 2) {
             TileItem *dst = tiles + pos_tile[a];
             uint32_t *kd = keys + pos_tile[a];
@@ -439,7 +450,7 @@ DevGraph host_descriptor(const bbc_graph *g, bool per_vertex, bool with_bounds) 
 void release_graph(bbc_graph *g, cudaStream_t st) {
     if (!g) return;
     void *ptrs[] = {g->rowS_off, g->rowS, g->rowC_off, g->rowC, g->permS, g->permC, g->wl, g->rng, g->anchor_of, g->bnd, g->boff,
-                    g->tile_items, g->warp_items, g->wt_items, g->dgraph, g->bS, g->bC,
+                    g->tile_items, g->warp_items, g->wt_items, g->gt_items, g->dgraph, g->bS, g->bC,
                     g->totals, g->queue};
     for (void *p : ptrs)
         if (p) dev_free(p, st);
@@ -456,6 +467,9 @@ bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
     if (g->wt_items) dev_free(g->wt_items, st);
     g->wt_items = nullptr;
     g->n_wt = 0;
+    if (g->gt_items) dev_free(g->gt_items, st);
+    g->gt_items = nullptr;
+    g->n_gt = 0;
     if (g->bnd) dev_free(g->bnd, st);
     if (g->boff) dev_free(g->boff, st);
     g->tile_items = nullptr;
@@ -472,37 +486,43 @@ bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
         return BBC_OK;
     }
     Scratch sc(st);
-    int32_t *nt = nullptr, *nh = nullptr, *nw = nullptr;
-    int64_t *pt = nullptr, *ph = nullptr, *pw = nullptr, *nb = nullptr;
+    int32_t *nt = nullptr, *nh = nullptr, *nw = nullptr, *ng = nullptr;
+    int64_t *pt = nullptr, *ph = nullptr, *pw = nullptr, *pg = nullptr, *nb = nullptr;
     BBC_TRY(sc.get(&nt, (size_t)nS));
     BBC_TRY(sc.get(&nh, (size_t)nS));
     BBC_TRY(sc.get(&nw, (size_t)nS));
+    BBC_TRY(sc.get(&ng, (size_t)nS));
     BBC_TRY(sc.get(&pt, (size_t)nS + 1));
     BBC_TRY(sc.get(&ph, (size_t)nS + 1));
     BBC_TRY(sc.get(&pw, (size_t)nS + 1));
+    BBC_TRY(sc.get(&pg, (size_t)nS + 1));
     BBC_TRY(sc.get(&nb, (size_t)nS));
     BBC_TRY(dev_alloc_n(&g->boff, (size_t)nS + 1, st));
     ClassifyParams P{g->nS, g->orient_low, t.tile_words, t.warp_max_wedges, t.split_wedges,
                      t.plain ? 0 : 1};
     note_launch();
-    k_classify<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, nt, nh, nb, nw);
+    k_classify<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, nt, nh, nb, nw, ng);
     BBC_LAUNCH_CHECK("k_classify");
     BBC_TRY(exclusive_scan_i32_to_i64(nt, pt, nS, st));
     BBC_TRY(exclusive_scan_i32_to_i64(nh, ph, nS, st));
     BBC_TRY(exclusive_scan_i32_to_i64(nw, pw, nS, st));
+    BBC_TRY(exclusive_scan_i32_to_i64(ng, pg, nS, st));
     BBC_TRY(exclusive_scan_i64(nb, g->boff, nS, st));
-    int64_t counts[4];
+    int64_t counts[5];
     BBC_CUDA_TRY(cudaMemcpyAsync(&counts[0], pt + nS, 8, cudaMemcpyDeviceToHost, st));
     BBC_CUDA_TRY(cudaMemcpyAsync(&counts[1], ph + nS, 8, cudaMemcpyDeviceToHost, st));
     BBC_CUDA_TRY(cudaMemcpyAsync(&counts[2], g->boff + nS, 8, cudaMemcpyDeviceToHost, st));
     BBC_CUDA_TRY(cudaMemcpyAsync(&counts[3], pw + nS, 8, cudaMemcpyDeviceToHost, st));
+    BBC_CUDA_TRY(cudaMemcpyAsync(&counts[4], pg + nS, 8, cudaMemcpyDeviceToHost, st));
     BBC_CUDA_TRY(cudaStreamSynchronize(st));
-    if (counts[3] > INT32_MAX) {
+    if (counts[3] > INT32_MAX || counts[4] > INT32_MAX) {
         set_error("work list longer than 2^31 items");
         return BBC_E_INVALID_ARG;
     }
     BBC_TRY(dev_alloc_n(&g->wt_items, (size_t)counts[3], st));
     g->n_wt = (int32_t)counts[3];
+    BBC_TRY(dev_alloc_n(&g->gt_items, (size_t)counts[4], st));
+    g->n_gt = (int32_t)counts[4];
     BBC_TRY(dev_alloc_n(&g->bnd, (size_t)counts[2], st));
     if (counts[2] > 0 && g->n_edges > 0) {
         note_launch();
@@ -524,8 +544,8 @@ bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
     BBC_TRY(dev_alloc_n(&g->tile_items, (size_t)ntile, st));
     g->n_tile = (int32_t)ntile;
     note_launch();
-    k_emit_items<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, pt, ph, pw, raw, keys,
-                                                     g->warp_items, g->wt_items);
+    k_emit_items<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, pt, ph, pw, pg, raw, keys,
+                                                     g->warp_items, g->wt_items, g->gt_items);
     BBC_LAUNCH_CHECK("k_emit_items");
     // Order the tile items by expected cost, largest first (the plain schedule keeps
     // rank order).

@@ -41,7 +41,7 @@ struct Request {
     std::vector<int8_t> s;
     size_t reserve = 0;          // device bytes reserved at admission
     bbc_graph *g = nullptr;
-    int32_t tile_done = 0, warp_done = 0, wt_done = 0;
+    int32_t tile_done = 0, warp_done = 0, wt_done = 0, gt_done = 0;
     bool done = false;
     bbc_status status = BBC_OK;
     uint64_t balanced = 0;
@@ -95,6 +95,8 @@ struct bbc_server {
     size_t warps_cap = 0;
     bbc::HashItem *wts = nullptr;
     size_t wts_cap = 0;
+    bbc::HashItem *gts = nullptr;
+    size_t gts_cap = 0;
     bbc::CopyJob *djobs = nullptr;
     size_t djobs_cap = 0;
     bbc::QueueState *queue_state = nullptr;
@@ -184,33 +186,40 @@ bbc_status run_tick(bbc_server *S, std::vector<Request *> &act) {
     const int chunk = 4 * device_sm_count() * S->tuning.blocks_per_sm;
     const size_t n = act.size();
     std::vector<DevGraph> hd(n);
-    std::vector<CopyJob> jt, jh, jw;
-    int64_t nt = 0, nh = 0, nw = 0;
-    std::vector<int32_t> take_t(n), take_h(n), take_w(n);
+    std::vector<CopyJob> jt, jh, jw, jg;
+    int64_t nt = 0, nh = 0, nw = 0, ngr = 0;
+    std::vector<int32_t> take_t(n), take_h(n), take_w(n), take_g(n);
     for (size_t i = 0; i < n; ++i) {
         bbc_graph *g = act[i]->g;
         hd[i] = host_descriptor(g, false, true);
         const int32_t rt = g->n_tile - act[i]->tile_done;
         const int32_t rh = g->n_warp - act[i]->warp_done;
         const int32_t rw = g->n_wt - act[i]->wt_done;
+        const int32_t rg = g->n_gt - act[i]->gt_done;
         take_t[i] = std::min(rt, chunk);
         take_h[i] = std::min(rh, 64 * chunk);
         take_w[i] = std::min(rw, 16 * chunk);
+        take_g[i] = std::min(rg, 4 * chunk);
         if (take_t[i] > 0)
             jt.push_back(CopyJob{g->tile_items + act[i]->tile_done, nt, take_t[i], (int32_t)i});
         if (take_h[i] > 0)
             jh.push_back(CopyJob{g->warp_items + act[i]->warp_done, nh, take_h[i], (int32_t)i});
         if (take_w[i] > 0)
             jw.push_back(CopyJob{g->wt_items + act[i]->wt_done, nw, take_w[i], (int32_t)i});
+        if (take_g[i] > 0)
+            jg.push_back(CopyJob{g->gt_items + act[i]->gt_done, ngr, take_g[i], (int32_t)i});
         nt += take_t[i];
         nh += take_h[i];
         nw += take_w[i];
+        ngr += take_g[i];
     }
     BBC_TRY(ensure(&S->dgraphs, &S->dgraphs_cap, n, st));
     BBC_TRY(ensure(&S->tiles, &S->tiles_cap, (size_t)std::max<int64_t>(nt, 1), st));
     BBC_TRY(ensure(&S->warps, &S->warps_cap, (size_t)std::max<int64_t>(nh, 1), st));
     BBC_TRY(ensure(&S->wts, &S->wts_cap, (size_t)std::max<int64_t>(nw, 1), st));
-    BBC_TRY(ensure(&S->djobs, &S->djobs_cap, std::max(jt.size(), std::max(jh.size(), jw.size())) + 1, st));
+    BBC_TRY(ensure(&S->gts, &S->gts_cap, (size_t)std::max<int64_t>(ngr, 1), st));
+    BBC_TRY(ensure(&S->djobs, &S->djobs_cap,
+                   std::max(std::max(jt.size(), jg.size()), std::max(jh.size(), jw.size())) + 1, st));
     if (!S->queue_state) BBC_TRY(dev_alloc_n(&S->queue_state, 1, st));
     if (S->host_totals_cap < 2 * n) {
         if (S->host_totals) cudaFreeHost(S->host_totals);
@@ -222,6 +231,7 @@ bbc_status run_tick(bbc_server *S, std::vector<Request *> &act) {
     BBC_TRY(concat_items(jt, true, S->tiles, S->djobs, st));
     BBC_TRY(concat_items(jh, false, S->warps, S->djobs, st));
     BBC_TRY(concat_items(jw, false, S->wts, S->djobs, st));
+    BBC_TRY(concat_items(jg, false, S->gts, S->djobs, st));
     BBC_CUDA_TRY(cudaMemsetAsync(S->queue_state, 0, sizeof(QueueState), st));
     CountLaunch L{};
     L.graphs = S->dgraphs;
@@ -231,6 +241,8 @@ bbc_status run_tick(bbc_server *S, std::vector<Request *> &act) {
     L.n_warp_items = (int32_t)nh;
     L.wt_items = S->wts;
     L.n_wt_items = (int32_t)nw;
+    L.gt_items = S->gts;
+    L.n_gt_items = (int32_t)ngr;
     L.queue = S->queue_state;
     L.tuning = S->tuning;
     BBC_TRY(launch_count(L, st));
@@ -238,6 +250,7 @@ bbc_status run_tick(bbc_server *S, std::vector<Request *> &act) {
         act[i]->tile_done += take_t[i];
         act[i]->warp_done += take_h[i];
         act[i]->wt_done += take_w[i];
+        act[i]->gt_done += take_g[i];
         BBC_CUDA_TRY(cudaMemcpyAsync(S->host_totals + 2 * i, act[i]->g->totals, 16,
                                      cudaMemcpyDeviceToHost, st));
     }
@@ -270,7 +283,7 @@ void worker_main(bbc_server *S) {
         for (size_t i = 0; i < act.size(); ++i) {
             Request *r = act[i];
             const bool complete = r->tile_done >= r->g->n_tile && r->warp_done >= r->g->n_warp &&
-                                  r->wt_done >= r->g->n_wt;
+                                  r->wt_done >= r->g->n_wt && r->gt_done >= r->g->n_gt;
             if (st != BBC_OK || complete) {
                 release_graph(r->g, S->stream);
                 r->g = nullptr;
@@ -445,7 +458,7 @@ void bbc_server_destroy(bbc_server *S) {
         r->g = nullptr;
         if (!r->done) finish_locked(S, r, BBC_E_CANCELLED, 0);
     }
-    void *bufs[] = {S->dgraphs, S->tiles, S->warps, S->wts, S->djobs, S->queue_state};
+    void *bufs[] = {S->dgraphs, S->tiles, S->warps, S->wts, S->gts, S->djobs, S->queue_state};
     for (void *p : bufs)
         if (p) dev_free(p, S->stream);
     cudaStreamSynchronize(S->stream);
