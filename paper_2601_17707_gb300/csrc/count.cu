@@ -58,6 +58,14 @@ __device__ __forceinline__ int64_t lower_bound_rank(const uint32_t *__restrict__
     return b;
 }
 
+// Fire-and-forget 64-bit add to global memory. The per-vertex and total counters are
+// reached through pointers loaded from the graph descriptor, which the compiler cannot
+// place in the global space, so atomicAdd there becomes a generic atomic that waits for
+// its old value; the explicit reduction does not.
+__device__ __forceinline__ void red_add(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.global.add.u64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "l"(v) : "memory");
+}
+
 __device__ __forceinline__ unsigned long long choose2(unsigned long long x) {
     return x * (x - (x > 0)) / 2;
 }
@@ -190,7 +198,7 @@ __device__ __forceinline__ void warp_sweep(const DevGraph &G, int64_t sb, int64_
             if ((uint32_t)lane < rest) visit(__ldg(rowC + s + head + 4 * m4 + lane));
             if (MODE == 1) {
                 acc = warp_sum(acc);
-                if (lane == j && acc) atomicAdd(G.bC + c, acc);
+                if (lane == j && acc) red_add(G.bC + c, acc);
             }
         }
         // Short slices: staged, then contiguous equal shares per lane.
@@ -255,7 +263,7 @@ __device__ __forceinline__ void warp_sweep(const DevGraph &G, int64_t sb, int64_
         }
         __syncwarp();
         if (MODE == 1) {
-            if (sl > 0 && sacc[lane]) atomicAdd(G.bC + c, (unsigned long long)sacc[lane]);
+            if (sl > 0 && sacc[lane]) red_add(G.bC + c, sacc[lane]);
             __syncwarp();
         }
     }
@@ -573,7 +581,7 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
             if (X.single)
                 centre_carry += mine;   // flushed once per item
             else if (mine)
-                atomicAdd(G.bC + (ent & kIdMask), mine);
+                red_add(G.bC + (ent & kIdMask), mine);
         }
     }
 }
@@ -584,7 +592,7 @@ __device__ __forceinline__ void pair_total(unsigned long long p, unsigned long l
     const unsigned long long f = choose2(p) + choose2(m);
     bal += f;
     unb += p * m;
-    if (bS && f) atomicAdd(bS + w, f);
+    if (bS && f) red_add(bS + w, f);
 }
 
 // Reads, reduces and clears the tile of endpoints [lo, hi). Words past the last
@@ -621,8 +629,8 @@ __device__ __forceinline__ void tile_epilogue(uint32_t *tile, uint32_t lo, uint3
                     const uint32_t lo16 = w4[k] & 0xffffu, hi16 = w4[k] >> 16;
                     const uint32_t f0 = (__dp4a(lo16, lo16, 0u) - __dp4a(lo16, 0x0101u, 0u)) >> 1;
                     const uint32_t f1 = (__dp4a(hi16, hi16, 0u) - __dp4a(hi16, 0x0101u, 0u)) >> 1;
-                    if (f0) atomicAdd(bS + lo + 8 * i + 2 * k, (unsigned long long)f0);
-                    if (f1) atomicAdd(bS + lo + 8 * i + 2 * k + 1, (unsigned long long)f1);
+                    if (f0) red_add(bS + lo + 8 * i + 2 * k, f0);
+                    if (f1) red_add(bS + lo + 8 * i + 2 * k + 1, f1);
                 }
             }
         } else if (CW == 1) {
@@ -634,7 +642,7 @@ __device__ __forceinline__ void tile_epilogue(uint32_t *tile, uint32_t lo, uint3
                 const uint32_t f = ((p * (p - (p > 0))) >> 1) + ((m * (m - (m > 0))) >> 1);
                 bal += f;
                 unb += p * m;
-                if (bS && f) atomicAdd(bS + lo + 4 * i + k, (unsigned long long)f);
+                if (bS && f) red_add(bS + lo + 4 * i + k, f);
             }
         } else {
             pair_total(q.x, q.y, bS, lo + 2 * i, bal, unb);
@@ -668,7 +676,7 @@ __device__ void run_tile_item(const DevGraph &G, const TileItem &item, int tile_
         tile_epilogue<CW>(tile, X.lo, X.hi, G.bS, bal, unb);
         __syncthreads();
     }
-    if (centre_carry) atomicAdd(G.bC + (cs.ent[threadIdx.x] & kIdMask), centre_carry);
+    if (centre_carry) red_add(G.bC + (cs.ent[threadIdx.x] & kIdMask), centre_carry);
 }
 
 // Persistent blocks pop (anchor, tile range) items, heaviest first.
@@ -716,9 +724,9 @@ k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, 
                 B += s_red[0][w];
                 U += s_red[1][w];
             }
-            if (B) atomicAdd(G.totals + 0, B);
-            if (U) atomicAdd(G.totals + 1, U);
-            if (G.bS && B) atomicAdd(G.bS + item.anchor, B);
+            if (B) red_add(G.totals + 0, B);
+            if (U) red_add(G.totals + 1, U);
+            if (G.bS && B) red_add(G.bS + item.anchor, B);
         }
     }
 }
@@ -770,16 +778,16 @@ k_warp_hash(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ it
             const unsigned long long f = choose2(p) + choose2(m);
             bal += f;
             unb += p * m;
-            if (G.bS && f) atomicAdd(G.bS + k, f);
+            if (G.bS && f) red_add(G.bS + k, f);
             keys[i] = kEmpty;
             vals[i] = 0;
         }
         bal = warp_sum(bal);
         unb = warp_sum(unb);
         if (lane == 0) {
-            if (bal) atomicAdd(G.totals + 0, bal);
-            if (unb) atomicAdd(G.totals + 1, unb);
-            if (G.bS && bal) atomicAdd(G.bS + a, bal);
+            if (bal) red_add(G.totals + 0, bal);
+            if (unb) red_add(G.totals + 1, unb);
+            if (G.bS && bal) red_add(G.bS + a, bal);
         }
         __syncwarp();
     }
@@ -847,9 +855,9 @@ __device__ void group_tile_item(const DevGraph &G, int a, uint32_t *tile, int gr
     bal = warp_sum(bal);
     unb = warp_sum(unb);
     if (lane == 0) {
-        if (bal) atomicAdd(G.totals + 0, bal);
-        if (unb) atomicAdd(G.totals + 1, unb);
-        if (G.bS && bal) atomicAdd(G.bS + a, bal);
+        if (bal) red_add(G.totals + 0, bal);
+        if (unb) red_add(G.totals + 1, unb);
+        if (G.bS && bal) red_add(G.bS + a, bal);
     }
     group_sync<GW>(grp);
 }

@@ -59,8 +59,14 @@ __global__ void k_validate_degrees(const int32_t *__restrict__ u, const int32_t 
             atomicOr(err, bad);
             continue;
         }
-        atomicAdd(deg_u + a, 1);
-        atomicAdd(deg_v + b, 1);
+        // lanes of one warp that hit the same vertex add once (edge lists sorted by one
+        // side put a hub's edges in consecutive lanes)
+        const unsigned act = __activemask();
+        const int lane = threadIdx.x & 31;
+        const unsigned mu = __match_any_sync(act, a);
+        if (lane == __ffs(mu) - 1) atomicAdd(deg_u + a, __popc(mu));
+        const unsigned mv = __match_any_sync(act, b);
+        if (lane == __ffs(mv) - 1) atomicAdd(deg_v + b, __popc(mv));
     }
 }
 
