@@ -54,6 +54,31 @@ def dist_env():
     return world, rank, local
 
 
+def rank_barrier(dist) -> None:
+    """All ranks meet here (no-op for a single process)."""
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The largest of the ranks' elapsed times for the same K steps: the job is done when
+    the slowest replica is. `device` holds the reduction tensor (cuda for NCCL, cpu for
+    gloo)."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank_step: float, steps: int, ms: float) -> float:
+    """Units processed by all ranks per second of the slowest rank's time (weak scaling:
+    every rank counts its own replica of the workload)."""
+    return world * units_per_rank_step * steps / (ms / 1e3)
+
+
 def hbm_peak():
     try:
         with open(PEAKS_FILE) as f:
@@ -348,12 +373,8 @@ def bench_gpu(args):
         torch.cuda.synchronize(dev)
         G.free()
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
     def timed(fn, steps):
-        barrier()
+        rank_barrier(dist)
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -362,13 +383,8 @@ def bench_gpu(args):
             fn()
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        barrier()
-        ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        rank_barrier(dist)
+        return max_over_ranks(e0.elapsed_time(e1), dist, dev)
 
     for _ in range(args.warmup):
         step_device()
@@ -387,7 +403,7 @@ def bench_gpu(args):
         for _ in range(max(1, args.warmup // 2)):
             step_host()
         ms_e2e = timed(step_host, args.steps)
-        e2e = {"value": world * W * args.steps / (ms_e2e / 1e3), "unit": UNIT,
+        e2e = {"value": whole_job_rate(world, W, args.steps, ms_e2e), "unit": UNIT,
                "h2d_bytes_per_step": g.n_edges * (4 + 4 + 1),
                "d2h_bytes_per_step": (g.n_u + g.n_v) * 8 + 16, "ms_per_step": ms_e2e / args.steps}
 
@@ -420,7 +436,7 @@ def bench_gpu(args):
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": world * W * args.steps / (ms / 1e3), "unit": UNIT,
+            "metric": METRIC, "value": whole_job_rate(world, W, args.steps, ms), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
