@@ -13,6 +13,11 @@ Contents:
 * ``brute_force``: Def. 1 and Def. 2 taken literally -- every (u, w, x, y) 4-tuple is
   tested for presence of all four edges and for an even number of negative edges.
   Pure Python, tiny graphs only.
+* ``motif``: the C oracle's sign classes (Sec. VII, Table 7) and balanced
+  (2,k)-bicliques (Def. 5) with the pairs on a chosen side.
+* ``brute_force_classes`` / ``brute_force_bicliques``: those two taken literally, by
+  enumerating 4-tuples (classified by the two centres' sign patterns) and every k-subset
+  of a pair's common neighbours (checked for an unbalanced butterfly). Tiny graphs only.
 * ``matrix_counts``: the signed/unsigned co-occurrence identity with a library
   matmul (numpy float64 BLAS; exact, since every product and partial sum is an
   integer of magnitude at most |V| < 2^53, then converted to int64). For the signed biadjacency A (entries +1, -1, 0) and
@@ -74,6 +79,9 @@ def _lib(mutant: int = 0) -> ctypes.CDLL:
             lib.bbco_count_sample.restype = ctypes.c_int
             lib.bbco_vertex.argtypes = [i32, i32, i64, p, p, p, ctypes.c_int, i32, p]
             lib.bbco_vertex.restype = ctypes.c_int
+            lib.bbco_motif.argtypes = [i32, i32, i64, p, p, p, ctypes.c_int, ctypes.c_uint32,
+                                       ctypes.c_int, p]
+            lib.bbco_motif.restype = ctypes.c_int
             lib.bbco_mutant.restype = ctypes.c_int
             _LIBS[mutant] = lib
         return _LIBS[mutant]
@@ -145,6 +153,75 @@ def vertex(g, side: int, x: int, mutant: int = 0) -> int:
     if st != 0:
         raise ValueError(f"oracle: {STATUS.get(st, st)}")
     return int(out.value)
+
+
+CLASS_NAMES = ("coherent ++/++", "coherent ++/--", "coherent --/--", "incoherent +-/+-",
+               "mixed ++/+-", "mixed +-/--")
+
+
+def _side(g, side: int):
+    """The edge arrays with the pair side first (side 0 = U, 1 = V)."""
+    u, v, s = _arrays(g)
+    if side == 0:
+        return g.n_u, g.n_v, u, v, s
+    return g.n_v, g.n_u, v, u, s
+
+
+def motif(g, kind: str, k: int = 2, side: int = 0, threads: int = 1, mutant: int = 0) -> tuple:
+    """kind "classes": the six sign-class totals in CLASS_NAMES order; kind "biclique":
+    (balanced (2,k)-bicliques, all (2,k)-bicliques). ``side`` holds the pair (the "2")."""
+    lib = _lib(mutant)
+    n_a, n_b, a, b, s = _side(g, side)
+    kind_id = {"classes": 1, "biclique": 2}[kind]
+    out = (ctypes.c_uint64 * 6)()
+    st = lib.bbco_motif(n_a, n_b, a.shape[0], a.ctypes.data, b.ctypes.data, s.ctypes.data,
+                        kind_id, int(k), int(threads), ctypes.addressof(out))
+    if st != 0:
+        raise ValueError(f"oracle: {STATUS.get(st, st)}")
+    return tuple(int(x) for x in out[:6 if kind_id == 1 else 2])
+
+
+def _sign_map(g, side: int):
+    n_a, n_b, a, b, s = _side(g, side)
+    return n_a, n_b, {(x, y): z for x, y, z in zip(a.tolist(), b.tolist(), s.tolist())}
+
+
+def brute_force_classes(g, side: int = 0) -> tuple:
+    """Every (u<w on the pair side, x<y on the other) 4-tuple with all four edges, put in
+    the class named by its two centres' sign patterns. Tiny graphs only."""
+    n_a, n_b, sign = _sign_map(g, side)
+    if n_a * n_b > 400:
+        raise ValueError("brute force is for graphs with |U|*|V| <= 400")
+
+    def kind(u, w, x):          # 0: both +, 1: both -, 2: the signs differ
+        su, sw = sign[(u, x)], sign[(w, x)]
+        return 2 if su != sw else (0 if su > 0 else 1)
+
+    index = {(0, 0): 0, (0, 1): 1, (1, 1): 2, (2, 2): 3, (0, 2): 4, (1, 2): 5}
+    out = [0] * 6
+    for u, w in itertools.combinations(range(n_a), 2):
+        for x, y in itertools.combinations(range(n_b), 2):
+            if all(e in sign for e in ((u, x), (u, y), (w, x), (w, y))):
+                out[index[tuple(sorted((kind(u, w, x), kind(u, w, y))))]] += 1
+    return tuple(out)
+
+
+def brute_force_bicliques(g, k: int, side: int = 0) -> tuple:
+    """(balanced, all) (2,k)-bicliques by enumeration: each k-subset of a pair's common
+    neighbours is a (2,k)-biclique, balanced when none of its butterflies holds an odd
+    number of negative edges (Def. 5 with Def. 2). Tiny graphs only."""
+    n_a, n_b, sign = _sign_map(g, side)
+    if n_a * n_b > 400:
+        raise ValueError("brute force is for graphs with |U|*|V| <= 400")
+    bal = total = 0
+    for u, w in itertools.combinations(range(n_a), 2):
+        common = [x for x in range(n_b) if (u, x) in sign and (w, x) in sign]
+        for sub in itertools.combinations(common, k):
+            total += 1
+            if all(sign[(u, x)] * sign[(u, y)] * sign[(w, x)] * sign[(w, y)] > 0
+                   for x, y in itertools.combinations(sub, 2)):
+                bal += 1
+    return bal, total
 
 
 def brute_force(g) -> Counts:

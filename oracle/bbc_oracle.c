@@ -26,7 +26,18 @@
  *     butterflies together with another same-type wedge of the pair, so it adds
  *     count_t(u,w) - 1 to b(v).
  *
- * Mutants: building with -DBBCO_MUTANT=k plants one plausible mistake (k = 1..7); the
+ * Motif counts (bbco_motif), the same wedge grouping with other per-pair sums:
+ *   - sign classes (Sec. VII, Table 7): for a pair {u, w} each common neighbour x is
+ *     "pp" (both edges +), "nn" (both -) or "a" (the signs differ). A butterfly is two
+ *     such centres, and its class is the unordered pair of centre kinds: coherent ++/++,
+ *     ++/--, --/--, incoherent +-/+-, mixed ++/+- and +-/--. Per pair these number
+ *     C(pp,2), pp*nn, C(nn,2), C(a,2), pp*a and nn*a;
+ *   - balanced (2,k)-bicliques (Def. 5, Algorithm 1): k common neighbours of the pair
+ *     with no unbalanced butterfly among them are all symmetric or all asymmetric
+ *     (Lemma 1), so the pair closes C(p,k) + C(n,k) balanced ones out of C(p+n,k).
+ *   Both depend on which side holds the pair; the anchors are side U here.
+ *
+ * Mutants: building with -DBBCO_MUTANT=k plants one plausible mistake (k = 1..9); the
  * pin tests compile those variants to show that each one fails at least one pin.
  */
 #include <stdint.h>
@@ -364,6 +375,161 @@ int bbco_vertex(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_t *eu, co
     adj_free(&a_other);
     if (total > (u128)UINT64_MAX) return BBCO_OVERFLOW;
     *out = (uint64_t)total;
+    return BBCO_OK;
+}
+
+/* C(m, k) exactly, or UINT64_MAX + 1 (as a u128) once it exceeds 2^64 - 1. Each step
+ * multiplies C(m, i) by (m - i) and divides by (i + 1), which is exact. */
+static u128 choose_k(uint64_t m, uint32_t k) {
+    const u128 too_big = (u128)UINT64_MAX + 1;
+    if (k > m) return 0;
+    if (k > m - k) k = (uint32_t)(m - k); /* C(m, k) = C(m, m - k): fewer, smaller steps */
+    u128 r = 1;
+    for (uint32_t i = 0; i < k; ++i) {
+#if BBCO_MUTANT == 9
+        r = r * (m - i) / (i + 2); /* mutant: divides by one too many */
+#else
+        r = r * (m - i) / (i + 1);
+#endif
+        if (r > (u128)UINT64_MAX) return too_big;
+    }
+    return r;
+}
+
+typedef struct {
+    const adj_t *au, *av;
+    int32_t n_u;
+    int kind;
+    uint32_t k;
+    int t, nt;
+    u128 out[6];
+    int overflow;
+} motif_job_t;
+
+static void *motif_worker(void *arg) {
+    motif_job_t *mj = (motif_job_t *)arg;
+    const adj_t *au = mj->au, *av = mj->av;
+    const int32_t n_u = mj->n_u;
+    /* per endpoint w: common neighbours by kind, and a touched list */
+    uint64_t *pp = (uint64_t *)calloc((size_t)n_u + 1, sizeof(uint64_t));
+    uint64_t *nn = (uint64_t *)calloc((size_t)n_u + 1, sizeof(uint64_t));
+    uint64_t *aa = (uint64_t *)calloc((size_t)n_u + 1, sizeof(uint64_t));
+    int32_t *touched = (int32_t *)malloc(((size_t)n_u + 1) * sizeof(int32_t));
+    if (!pp || !nn || !aa || !touched) {
+        free(pp);
+        free(nn);
+        free(aa);
+        free(touched);
+        mj->overflow = -1;
+        return NULL;
+    }
+    for (int32_t u = mj->t; u < n_u; u += mj->nt) {
+        int32_t n_touched = 0;
+        for (int64_t i = au->off[u]; i < au->off[u + 1]; ++i) {
+            const int32_t x = au->nbr[i];
+            const int8_t su = au->sgn[i];
+            for (int64_t j = av->off[x]; j < av->off[x + 1]; ++j) {
+                const int32_t w = av->nbr[j];
+                if (w <= u) continue; /* each unordered pair once */
+                const int8_t sw = av->sgn[j];
+                if (pp[w] == 0 && nn[w] == 0 && aa[w] == 0) touched[n_touched++] = w;
+#if BBCO_MUTANT == 8
+                if (su == sw) /* mutant: both-negative centres counted as pp */
+#else
+                if (su == sw && su > 0)
+#endif
+                    pp[w]++;
+                else if (su == sw)
+                    nn[w]++;
+                else
+                    aa[w]++;
+            }
+        }
+        for (int32_t q = 0; q < n_touched; ++q) {
+            const int32_t w = touched[q];
+            const uint64_t a = pp[w], b = nn[w], c = aa[w];
+            if (mj->kind == 1) {
+                mj->out[0] += choose2(a);
+                mj->out[1] += (u128)a * b;
+                mj->out[2] += choose2(b);
+                mj->out[3] += choose2(c);
+                mj->out[4] += (u128)a * c;
+                mj->out[5] += (u128)b * c;
+            } else {
+                const u128 cp = choose_k(a + b, mj->k), cn = choose_k(c, mj->k);
+                const u128 call = choose_k(a + b + c, mj->k);
+                if (cp > (u128)UINT64_MAX || cn > (u128)UINT64_MAX || call > (u128)UINT64_MAX)
+                    mj->overflow = 1;
+                else {
+                    mj->out[0] += cp + cn;
+                    mj->out[1] += call;
+                }
+            }
+            pp[w] = nn[w] = aa[w] = 0;
+        }
+    }
+    free(pp);
+    free(nn);
+    free(aa);
+    free(touched);
+    return NULL;
+}
+
+/*
+ * Motif totals with the pairs on side U (swap the edge arrays for side V).
+ * kind 1: the six sign classes, out[0..5] in the order of Table 7.
+ * kind 2: out[0] = balanced (2,k)-bicliques, out[1] = all (2,k)-bicliques, k >= 2.
+ * Returns BBCO_OVERFLOW when a total (or one pair's binomial) exceeds 2^64 - 1.
+ */
+int bbco_motif(int32_t n_u, int32_t n_v, int64_t n_edges, const int32_t *eu, const int32_t *ev,
+               const int8_t *es, int kind, uint32_t k, int n_threads, uint64_t *out) {
+    int st = check_input(n_u, n_v, n_edges, eu, ev, es);
+    if (st) return st;
+    if ((kind != 1 && kind != 2) || (kind == 2 && k < 2) || !out) return BBCO_BAD_INPUT;
+    if (n_threads < 1) n_threads = 1;
+    adj_t au, av;
+    if (adj_build(n_u, n_edges, eu, ev, es, &au)) return BBCO_NO_MEMORY;
+    if (adj_build(n_v, n_edges, ev, eu, es, &av)) {
+        adj_free(&au);
+        return BBCO_NO_MEMORY;
+    }
+    motif_job_t *jobs = (motif_job_t *)calloc((size_t)n_threads, sizeof(motif_job_t));
+    pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
+    if (!jobs || !th) {
+        free(jobs);
+        free(th);
+        adj_free(&au);
+        adj_free(&av);
+        return BBCO_NO_MEMORY;
+    }
+    for (int t = 0; t < n_threads; ++t) {
+        jobs[t].au = &au;
+        jobs[t].av = &av;
+        jobs[t].n_u = n_u;
+        jobs[t].kind = kind;
+        jobs[t].k = k;
+        jobs[t].t = t;
+        jobs[t].nt = n_threads;
+    }
+    for (int t = 1; t < n_threads; ++t) pthread_create(&th[t], NULL, motif_worker, &jobs[t]);
+    motif_worker(&jobs[0]);
+    for (int t = 1; t < n_threads; ++t) pthread_join(th[t], NULL);
+    u128 tot[6] = {0, 0, 0, 0, 0, 0};
+    int overflow = 0, nomem = 0;
+    for (int t = 0; t < n_threads; ++t) {
+        for (int i = 0; i < 6; ++i) tot[i] += jobs[t].out[i];
+        if (jobs[t].overflow > 0) overflow = 1;
+        if (jobs[t].overflow < 0) nomem = 1;
+    }
+    free(jobs);
+    free(th);
+    adj_free(&au);
+    adj_free(&av);
+    if (nomem) return BBCO_NO_MEMORY;
+    for (int i = 0; i < 6; ++i)
+        if (tot[i] > (u128)UINT64_MAX) overflow = 1;
+    if (overflow) return BBCO_OVERFLOW;
+    for (int i = 0; i < 6; ++i) out[i] = (uint64_t)tot[i];
     return BBCO_OK;
 }
 
