@@ -155,6 +155,37 @@ bbc_status bbc_count_async(bbc_graph *g, uint64_t *totals_dev, uint64_t *per_u,
  */
 bbc_status bbc_count_noalloc(const bbc_graph *g, uint64_t *totals_dev, void *cuda_stream);
 
+/* Motif kinds of bbc_count_motif. */
+enum {
+    BBC_MOTIF_SIGN_CLASSES = 1, /* the six sign classes of Sec. VII, Table 7 */
+    BBC_MOTIF_BICLIQUE_2K = 2   /* balanced (2,k)-bicliques, Def. 5 */
+};
+
+/*
+ * bbc_count_motif -- other per-pair sums over the same wedge grouping, with the pair
+ * ("2") on the graph's pair side S: prepare with BBC_SIDE_FORCE_U or BBC_SIDE_FORCE_V
+ * to fix it, since neither motif is side-symmetric (bbc_graph_info reports S).
+ *
+ *   kind BBC_MOTIF_SIGN_CLASSES (Sec. VII, Table 7; k ignored): for a pair {a, w} of S
+ *     each common neighbour c is pp (both edges +), nn (both -) or a (signs differ);
+ *     out[0..5] = the numbers of butterflies of each class, in Table 7's order:
+ *     coherent ++/++ = sum C(pp,2), coherent ++/-- = sum pp*nn, coherent --/-- =
+ *     sum C(nn,2), incoherent +-/+- = sum C(a,2), mixed ++/+- = sum pp*a, mixed
+ *     +-/-- = sum nn*a. The first four add up to bbc_count's balanced total, the last
+ *     two to its unbalanced one.
+ *   kind BBC_MOTIF_BICLIQUE_2K (Def. 5 with Algorithm 1's C(., k) aggregation; k >= 2):
+ *     out[0] = balanced (2,k)-bicliques = sum C(p,k) + C(n,k) (k common neighbours
+ *     with no unbalanced butterfly among them are all symmetric or all asymmetric, by
+ *     Lemma 1); out[1] = all (2,k)-bicliques = sum C(p+n,k). k = 2 gives bbc_count's
+ *     balanced total and the unsigned butterfly count.
+ *   out   host uint64[6] (classes) or uint64[2] (bicliques). Overwritten.
+ * Errors: BBC_E_INVALID_ARG (kind, k < 2 or k >= 2^31, NULL), BBC_E_OVERFLOW_RISK when
+ * a sum or a single binomial exceeds 2^64 - 1. The call rebuilds the graph's work lists
+ * for the motif (all anchors on block tiles) and synchronises `cuda_stream`; the next
+ * bbc_count rebuilds its own lists.
+ */
+bbc_status bbc_count_motif(bbc_graph *g, int32_t kind, int32_t k, uint64_t *out, void *cuda_stream);
+
 /*
  * bbc_graph_info -- facts about a prepared graph (any output pointer may be NULL).
  *   side          0 when U is the pair side S, 1 when V is.

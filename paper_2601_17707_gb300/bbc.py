@@ -37,8 +37,11 @@ EXPORTS = (
     "bbc_graph_free", "bbc_count_batch", "bbc_autotune_batch", "bbc_server_create", "bbc_submit",
     "bbc_poll", "bbc_wait", "bbc_server_stats", "bbc_server_destroy", "bbc_status_string",
     "bbc_last_error", "bbc_launch_count", "bbc_profile_start", "bbc_profile_stop",
-    "bbc_count_noalloc",
+    "bbc_count_noalloc", "bbc_count_motif",
 )
+
+MOTIF_SIGN_CLASSES = 1
+MOTIF_BICLIQUE_2K = 2
 
 
 class BBCError(RuntimeError):
@@ -107,6 +110,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "bbc_profile_stop": ([ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)], ctypes.c_int),
             "bbc_last_error": ([], ctypes.c_char_p),
             "bbc_count_noalloc": ([vp, vp, vp], ctypes.c_int),
+            "bbc_count_motif": ([vp, i32, i32, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -262,6 +266,16 @@ class Graph:
                                  ctypes.byref(tuning) if tuning is not None else None,
                                  _stream_ptr(stream))
         check(st, "bbc_count_async")
+
+    def count_motif(self, kind: str, k: int = 2, stream=None) -> tuple:
+        """kind "classes": the six sign-class counts (Table 7's order); kind "biclique":
+        (balanced (2,k)-bicliques, all (2,k)-bicliques). The pair side is the graph's S."""
+        lib = load()
+        kind_id = {"classes": MOTIF_SIGN_CLASSES, "biclique": MOTIF_BICLIQUE_2K}[kind]
+        out = (ctypes.c_uint64 * 6)()
+        check(lib.bbc_count_motif(self.handle, kind_id, int(k), ctypes.addressof(out),
+                                  _stream_ptr(stream)), "bbc_count_motif")
+        return tuple(int(x) for x in out[:6 if kind_id == MOTIF_SIGN_CLASSES else 2])
 
     def info(self) -> Info:
         lib = load()

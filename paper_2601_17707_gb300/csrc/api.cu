@@ -359,6 +359,71 @@ bbc_status bbc_count(bbc_graph *g, uint64_t *balanced, uint64_t *unbalanced, uin
     }
 }
 
+bbc_status bbc_count_motif(bbc_graph *g, int32_t kind, int32_t k, uint64_t *out, void *cuda_stream) {
+    if (!g || !out) {
+        set_error("bbc_count_motif: NULL graph or NULL output");
+        return BBC_E_INVALID_ARG;
+    }
+    if (kind != BBC_MOTIF_SIGN_CLASSES && kind != BBC_MOTIF_BICLIQUE_2K) {
+        set_error("bbc_count_motif: unknown motif kind");
+        return BBC_E_INVALID_ARG;
+    }
+    if (kind == BBC_MOTIF_BICLIQUE_2K && (k < 2 || k == INT32_MAX)) {
+        set_error("bbc_count_motif: k must lie in [2, 2^31 - 2]");
+        return BBC_E_INVALID_ARG;
+    }
+    try {
+        cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+        const int sms = device_sm_count();
+        Tuning T = resolve_tuning(nullptr, sms);
+        T.split_wedges = auto_split(g->wedges, sms, T.blocks_per_sm);
+        T.warp_max_wedges = 0;  // no hash path: every anchor with wedges is a tile item
+        T.tiles_only = 1;
+        const int smem_words = T.tile_words;
+        // class counters take twice the words per endpoint: the lists see half the tile
+        if (kind == BBC_MOTIF_SIGN_CLASSES) T.tile_words = smem_words / 2;
+        BBC_TRY(build_work_lists(g, T, st));
+        unsigned long long *dout = nullptr;
+        BBC_TRY(dev_alloc_n(&dout, 8, st));
+        bbc_status rc = BBC_OK;
+        unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        do {
+            cudaError_t e = cudaMemsetAsync(dout, 0, 64, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(g->queue, 0, sizeof(QueueState), st);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "bbc_count_motif");
+                break;
+            }
+            DevGraph d = host_descriptor(g, false, true);
+            note_launch();
+            k_store_descriptor<<<1, 1, 0, st>>>(d, g->dgraph);
+            if ((e = cudaGetLastError()) != cudaSuccess) {
+                rc = cuda_fail(e, "bbc_count_motif");
+                break;
+            }
+            const int blocks = std::max(1, std::min(g->n_tile, sms * T.blocks_per_sm));
+            rc = launch_motif(g->dgraph, g->tile_items, g->n_tile, &g->queue->tile_head, kind, k,
+                              smem_words, blocks, dout, st);
+            if (rc != BBC_OK) break;
+            e = cudaMemcpyAsync(h, dout, 64, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) rc = cuda_fail(e, "bbc_count_motif");
+        } while (false);
+        dev_free(dout, st);
+        if (rc != BBC_OK) return rc;
+        if (h[7]) {
+            set_error("bbc_count_motif: a count exceeds 2^64 - 1");
+            return BBC_E_OVERFLOW_RISK;
+        }
+        const int n_out = kind == BBC_MOTIF_SIGN_CLASSES ? 6 : 2;
+        for (int j = 0; j < n_out; ++j) out[j] = h[j];
+        return BBC_OK;
+    } catch (...) {
+        set_error("unexpected exception in bbc_count_motif");
+        return BBC_E_CUDA;
+    }
+}
+
 unsigned long long bbc_launch_count(void) { return g_launches.load(); }
 
 bbc_status bbc_profile_start(void) {

@@ -97,9 +97,17 @@ struct Tuning {
     long long split_wedges;
     int blocks_per_sm;
     int plain;                 // static one-block-per-anchor schedule (Algorithm 3)
+    int tiles_only = 0;        // every anchor on block tiles (no hash or warp/group tiles)
 };
 
 Tuning resolve_tuning(const bbc_tuning *t, int sm_count);
+
+// Motif counts over a graph's tile items (built with tiles_only): kind 1 the six sign
+// classes, kind 2 balanced and all (2,k)-bicliques. out (device, 8 words, zeroed by the
+// caller): the sums, then an overflow flag in word 7.
+bbc_status launch_motif(const DevGraph *graph, const TileItem *items, int n_items, unsigned *head,
+                        int kind, int k, int tile_words, int blocks, unsigned long long *out,
+                        cudaStream_t st);
 
 // ----------------------------------------------------------------------------- errors
 

@@ -294,6 +294,53 @@ struct TileCounter {
         if (CW == 1) return (tile[e] >> (t << 4)) & 0xffffu;
         return tile[2 * e + t];
     }
+    // a C -> S entry x (endpoint rank | sign << 31) reached through an anchor edge of
+    // sign bit sg: the wedge is symmetric (t = 0) or asymmetric (t = 1)
+    __device__ __forceinline__ void bump_entry(uint32_t x, uint32_t sg) const {
+        bump(x & kIdMask, (x ^ sg) >> 31);
+    }
+    __device__ __forceinline__ uint32_t peek_entry(uint32_t x, uint32_t sg) const {
+        return peek(x & kIdMask, (x ^ sg) >> 31);
+    }
+};
+
+// Sign-class counters (Sec. VII): per endpoint the centres whose two edges are both +
+// (kind 0), both - (kind 1), or of different signs (kind 2). CW 0: one word of bytes
+// (pp, nn, a, 0); CW 1: two words (pp | nn << 16, a); CW 2: four 32-bit words. An
+// endpoint takes twice the words of TileCounter's layout.
+template <int CW>
+struct ClassCounter {
+    uint32_t *tile;
+    uint32_t lo;
+    __device__ __forceinline__ void bump_entry(uint32_t x, uint32_t sg) const {
+        const uint32_t e = (x & kIdMask) - lo;
+        const uint32_t kind = ((x ^ sg) >> 31) ? 2u : (sg >> 31);
+        if (CW == 0)
+            atomicAdd(tile + e, 1u << (kind << 3));
+        else if (CW == 1)
+            atomicAdd(tile + 2 * e + (kind >> 1), kind == 2 ? 1u : 1u << (kind << 4));
+        else
+            atomicAdd(tile + 4 * e + kind, 1u);
+    }
+    __device__ __forceinline__ uint32_t peek_entry(uint32_t, uint32_t) const { return 1u; }
+    __device__ __forceinline__ void read(uint32_t e, uint32_t &pp, uint32_t &nn, uint32_t &a) const {
+        if (CW == 0) {
+            const uint32_t v = tile[e];
+            pp = v & 0xffu;
+            nn = (v >> 8) & 0xffu;
+            a = (v >> 16) & 0xffu;
+        } else if (CW == 1) {
+            const uint32_t v = tile[2 * e];
+            pp = v & 0xffffu;
+            nn = v >> 16;
+            a = tile[2 * e + 1];
+        } else {
+            pp = tile[4 * e];
+            nn = tile[4 * e + 1];
+            a = tile[4 * e + 2];
+        }
+    }
+    static constexpr uint32_t words_per_endpoint = CW == 0 ? 1u : (CW == 1 ? 2u : 4u);
 };
 
 __host__ __device__ constexpr uint32_t endpoints_per_tile(int cw, uint32_t tile_words) {
@@ -367,14 +414,12 @@ __device__ __forceinline__ uint32_t warp_sum32(uint32_t x) {
 __device__ __forceinline__ unsigned long long warp_sum_acc(unsigned long long x) { return warp_sum(x); }
 __device__ __forceinline__ uint32_t warp_sum_acc(uint32_t x) { return warp_sum32(x); }
 
-template <int MODE, int CW>
-__device__ __forceinline__ void wedge(const TileCounter<CW> &ctr, uint32_t x, uint32_t sg,
-                                      Acc<CW> &acc) {
-    const uint32_t t = (x ^ sg) >> 31;
+template <int MODE, int CW, class Ctr>
+__device__ __forceinline__ void wedge(const Ctr &ctr, uint32_t x, uint32_t sg, Acc<CW> &acc) {
     if (MODE == 0)
-        ctr.bump(x & kIdMask, t);
+        ctr.bump_entry(x, sg);
     else
-        acc += ctr.peek(x & kIdMask, t) - 1u;
+        acc += ctr.peek_entry(x, sg) - 1u;
 }
 
 // First index of row[b, lim) whose rank is >= key (the row is sorted by rank), found by
@@ -450,10 +495,9 @@ __device__ __forceinline__ unsigned long long acc_get(ChunkSmem &cs, int j) {
 // that warps pull from a shared counter and sweep with coalesced 16-byte loads. MODE 0
 // bumps the counters; MODE 1 reads them and adds (count - 1) per wedge to the centre's
 // per-vertex sum. A single-chunk MODE 1 pass reuses the slices MODE 0 just found.
-template <int MODE, int CW>
+template <int MODE, int CW, class Ctr>
 __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const SweepCtx &X,
-                            const TileCounter<CW> &ctr, ChunkSmem &cs,
-                            unsigned long long &centre_carry) {
+                            const Ctr &ctr, ChunkSmem &cs, unsigned long long &centre_carry) {
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t *__restrict__ rowC = G.rowC;
     for (int64_t cb = sb; cb < se; cb += kChunk) {
@@ -518,7 +562,7 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
                         }
                         x2 = __ldg(rowC + (uint32_t)(base2 + k2));
                     }
-                    wedge<MODE>(ctr, x, sg, acc);
+                    wedge<MODE, CW>(ctr, x, sg, acc);
                     if (k2 >= k1) break;
                     if (MODE == 1 && j2 != j && acc) {
                         acc_add<CW>(cs, j, acc);
@@ -548,7 +592,7 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
                 const uint32_t sg = cs.ent[j] & kSignBit;
                 Acc<CW> acc = 0;
                 const uint32_t head = min(n, (4u - (s & 3u)) & 3u);
-                if ((uint32_t)lane < head) wedge<MODE>(ctr, __ldg(rowC + s + lane), sg, acc);
+                if ((uint32_t)lane < head) wedge<MODE, CW>(ctr, __ldg(rowC + s + lane), sg, acc);
                 const uint32_t m4 = (n - head) >> 2;
                 const uint4 *v4 = reinterpret_cast<const uint4 *>(rowC + s + head);
                 // two 16-byte loads in flight per lane
@@ -556,19 +600,19 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
                     const uint4 xa = __ldg(v4 + q);
                     const bool has_b = q + 32 < m4;
                     const uint4 xb = has_b ? __ldg(v4 + q + 32) : make_uint4(0u, 0u, 0u, 0u);
-                    wedge<MODE>(ctr, xa.x, sg, acc);
-                    wedge<MODE>(ctr, xa.y, sg, acc);
-                    wedge<MODE>(ctr, xa.z, sg, acc);
-                    wedge<MODE>(ctr, xa.w, sg, acc);
+                    wedge<MODE, CW>(ctr, xa.x, sg, acc);
+                    wedge<MODE, CW>(ctr, xa.y, sg, acc);
+                    wedge<MODE, CW>(ctr, xa.z, sg, acc);
+                    wedge<MODE, CW>(ctr, xa.w, sg, acc);
                     if (has_b) {
-                        wedge<MODE>(ctr, xb.x, sg, acc);
-                        wedge<MODE>(ctr, xb.y, sg, acc);
-                        wedge<MODE>(ctr, xb.z, sg, acc);
-                        wedge<MODE>(ctr, xb.w, sg, acc);
+                        wedge<MODE, CW>(ctr, xb.x, sg, acc);
+                        wedge<MODE, CW>(ctr, xb.y, sg, acc);
+                        wedge<MODE, CW>(ctr, xb.z, sg, acc);
+                        wedge<MODE, CW>(ctr, xb.w, sg, acc);
                     }
                 }
                 const uint32_t rest = (n - head) & 3u;
-                if ((uint32_t)lane < rest) wedge<MODE>(ctr, __ldg(rowC + s + head + 4 * m4 + lane), sg, acc);
+                if ((uint32_t)lane < rest) wedge<MODE, CW>(ctr, __ldg(rowC + s + head + 4 * m4 + lane), sg, acc);
                 if (MODE == 1) {
                     acc = warp_sum_acc(acc);
                     if (lane == 0 && acc) acc_add<CW>(cs, j, acc);
@@ -671,8 +715,8 @@ __device__ void run_tile_item(const DevGraph &G, const TileItem &item, int tile_
         X.lo = X.range_lo + (uint32_t)t * ept;
         X.hi = min(X.lo + ept, X.range_hi);
         const TileCounter<CW> ctr{tile, X.lo};
-        block_sweep<0>(G, sb, se, X, ctr, cs, centre_carry);
-        if (G.bC) block_sweep<1>(G, sb, se, X, ctr, cs, centre_carry);
+        block_sweep<0, CW>(G, sb, se, X, ctr, cs, centre_carry);
+        if (G.bC) block_sweep<1, CW>(G, sb, se, X, ctr, cs, centre_carry);
         tile_epilogue<CW>(tile, X.lo, X.hi, G.bS, bal, unb);
         __syncthreads();
     }
@@ -891,6 +935,165 @@ k_group_tile(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ i
     }
 }
 
+// ----------------------------------------------------------------------------- motifs
+
+// C(m, k) for k < 2^31: each step multiplies C(m, i) by (m - i) and divides by i + 1,
+// which is exact; the 128-bit product is divided in 32-bit digits. Sets ovf and returns 0
+// once the value passes 2^64 - 1.
+__device__ unsigned long long choose_k(unsigned long long m, uint32_t k, unsigned &ovf) {
+    if (k > m) return 0;
+    if (k > m - k) k = (uint32_t)(m - k);
+    unsigned long long r = 1;
+    for (uint32_t i = 0; i < k; ++i) {
+        const unsigned long long f = m - i, d = (unsigned long long)i + 1;
+        const unsigned long long hi = __umul64hi(r, f), lo = r * f;
+        if (hi >= d) {  // the quotient needs more than 64 bits
+            ovf = 1;
+            return 0;
+        }
+        const unsigned long long t1 = (hi << 32) | (lo >> 32);
+        const unsigned long long q1 = t1 / d, r1 = t1 % d;
+        const unsigned long long t0 = (r1 << 32) | (lo & 0xffffffffull);
+        r = (q1 << 32) | (t0 / d);
+    }
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long add_ovf(unsigned long long a, unsigned long long b,
+                                                      unsigned &ovf) {
+    const unsigned long long s = a + b;
+    if (s < a) ovf = 1;
+    return s;
+}
+
+// Sign classes of the endpoints [0, n) of a class tile (Table 7's six rows), then clears
+// the tile. The sums are bounded by the graph's butterfly count, which preparation
+// checked to fit 64 bits.
+template <int CW>
+__device__ void class_epilogue(const ClassCounter<CW> &ctr, uint32_t n, unsigned long long (&acc)[6]) {
+    for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
+        uint32_t pp, nn, a;
+        ctr.read(e, pp, nn, a);
+        if ((pp | nn | a) == 0) continue;
+        acc[0] += choose2(pp);
+        acc[1] += (unsigned long long)pp * nn;
+        acc[2] += choose2(nn);
+        acc[3] += choose2(a);
+        acc[4] += (unsigned long long)pp * a;
+        acc[5] += (unsigned long long)nn * a;
+    }
+    __syncthreads();
+    const uint32_t words = n * ClassCounter<CW>::words_per_endpoint;
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) ctr.tile[i] = 0;
+}
+
+// Balanced and all (2,k)-bicliques of the endpoints [lo, hi) of a counter tile:
+// C(p,k) + C(n,k) and C(p+n,k) per endpoint (Lemma 1 extended to k centres), then clears
+// the tile.
+template <int CW>
+__device__ void biclique_epilogue(const TileCounter<CW> &ctr, uint32_t lo, uint32_t hi, uint32_t k,
+                                  unsigned long long (&acc)[6], unsigned &ovf) {
+    const uint32_t n = hi - lo;
+    for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
+        const unsigned long long p = ctr.peek(lo + e, 0), m = ctr.peek(lo + e, 1);
+        if (p + m < k) continue;
+        const unsigned long long bal = add_ovf(choose_k(p, k, ovf), choose_k(m, k, ovf), ovf);
+        acc[0] = add_ovf(acc[0], bal, ovf);
+        acc[1] = add_ovf(acc[1], choose_k(p + m, k, ovf), ovf);
+    }
+    __syncthreads();
+    const uint32_t words = CW == 0 ? (n + 1) / 2 : (CW == 1 ? n : 2 * n);
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) ctr.tile[i] = 0;
+}
+
+// One (anchor, tile range) item of a motif count: the count sweep of the tile kernel
+// with the motif's counters, then the motif's epilogue. tile_words is the item lists'
+// tile size: class tiles use twice the words per endpoint, so their lists are built
+// for half the shared-memory tile.
+template <int KIND, int CW>
+__device__ void run_motif_item(const DevGraph &G, const TileItem &item, int tile_words, uint32_t *tile,
+                               ChunkSmem &cs, uint32_t k, unsigned long long (&acc)[6], unsigned &ovf) {
+    const int a = item.anchor;
+    const int64_t sb = G.rowS_off[a], se = G.rowS_off[a + 1];
+    const uint32_t ept = endpoints_per_tile(CW, (uint32_t)tile_words);
+    SweepCtx X;
+    X.range_lo = G.orient_low ? 0u : (uint32_t)a + 1u;
+    X.range_hi = G.orient_low ? (uint32_t)a : (uint32_t)G.nS;
+    const int t0 = item.tile_begin, t1 = tile_end_of(item);
+    X.nt = (int)((X.range_hi - X.range_lo + ept - 1) / ept);
+    X.single = se - sb <= kChunk;
+    X.deg = se - sb;
+    X.bbase = G.boff ? G.boff[a] : 0;
+    unsigned long long carry = 0;  // unused: no centre pass
+    for (int t = t0; t < t1; ++t) {
+        X.t = t;
+        X.lo = X.range_lo + (uint32_t)t * ept;
+        X.hi = min(X.lo + ept, X.range_hi);
+        if (KIND == 1) {
+            const ClassCounter<CW> ctr{tile, X.lo};
+            block_sweep<0, CW>(G, sb, se, X, ctr, cs, carry);
+            class_epilogue<CW>(ctr, X.hi - X.lo, acc);
+        } else {
+            const TileCounter<CW> ctr{tile, X.lo};
+            block_sweep<0, CW>(G, sb, se, X, ctr, cs, carry);
+            biclique_epilogue<CW>(ctr, X.lo, X.hi, k, acc, ovf);
+        }
+        __syncthreads();
+    }
+}
+
+// Persistent blocks over the motif item list (kind 1: sign classes into out[0..5];
+// kind 2: balanced and all (2,k)-bicliques into out[0..1]); out[7] != 0 reports a sum
+// past 2^64 - 1.
+template <int KIND>
+__global__ void __launch_bounds__(kTileThreads, 2)
+k_tile_motif(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, int n_items,
+             unsigned *head, int list_tile_words, int tile_words, uint32_t k,
+             unsigned long long *out) {
+    extern __shared__ uint4 smem_tile[];
+    uint32_t *tile = reinterpret_cast<uint32_t *>(smem_tile);
+    __shared__ ChunkSmem cs;
+    __shared__ int s_item;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < tile_words; i += blockDim.x) tile[i] = 0;
+    unsigned long long acc[6] = {0, 0, 0, 0, 0, 0};
+    unsigned ovf = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const TileItem item = items[it];
+        const DevGraph &G = graphs[item.graph];
+        switch (tile_width_of(item)) {
+            case 0: run_motif_item<KIND, 0>(G, item, list_tile_words, tile, cs, k, acc, ovf); break;
+            case 1: run_motif_item<KIND, 1>(G, item, list_tile_words, tile, cs, k, acc, ovf); break;
+            default: run_motif_item<KIND, 2>(G, item, list_tile_words, tile, cs, k, acc, ovf); break;
+        }
+        __syncthreads();
+    }
+    // block sums (through the chunk accumulator, idle now), then one add per sum
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        unsigned long long v = acc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = add_ovf(v, __shfl_xor_sync(kFull, v, o), ovf);
+        if (lane == 0) cs.acc[warp * 6 + i] = v;
+    }
+    const int any_ovf = __syncthreads_or((int)ovf);
+    if (threadIdx.x < 6) {
+        unsigned o2 = 0;
+        unsigned long long v = 0;
+        for (int w = 0; w < kTileWarps; ++w) v = add_ovf(v, cs.acc[w * 6 + threadIdx.x], o2);
+        if (v) {
+            const unsigned long long old = atomicAdd(out + threadIdx.x, v);
+            if (old + v < old) o2 = 1;
+        }
+        if (o2) atomicOr(out + 7, 1ull);
+    }
+    if (threadIdx.x == 0 && any_ovf) atomicOr(out + 7, 1ull);
+}
+
 }  // namespace
 
 bbc_status configure_count_kernels() {
@@ -908,6 +1111,16 @@ bbc_status configure_count_kernels() {
         BBC_CUDA_TRY(cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         BBC_CUDA_TRY(cudaFuncSetAttribute(k_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           maxopt - (int)fa.sharedSizeBytes));
+        for (const void *f : {(const void *)k_tile_motif<1>, (const void *)k_tile_motif<2>}) {
+            cudaFuncAttributes fm{};
+            BBC_CUDA_TRY(cudaFuncGetAttributes(&fm, f));
+            if ((int)fm.sharedSizeBytes > tile_static_smem_bytes()) {
+                set_error("motif kernel static shared memory exceeds its budget");
+                return BBC_E_CUDA;
+            }
+            BBC_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              maxopt - (int)fm.sharedSizeBytes));
+        }
         BBC_CUDA_TRY(cudaFuncSetAttribute(k_warp_hash, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           kHashWarps * 2 * kHashSlots * 4));
         BBC_CUDA_TRY(cudaFuncSetAttribute(k_group_tile<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -963,6 +1176,23 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
         BBC_CUDA_TRY(cudaGetLastError());
         profile_end(tok, st);
     }
+    return BBC_OK;
+}
+
+bbc_status launch_motif(const DevGraph *graph, const TileItem *items, int n_items, unsigned *head,
+                        int kind, int k, int tile_words, int blocks, unsigned long long *out,
+                        cudaStream_t st) {
+    BBC_TRY(configure_count_kernels());
+    if (n_items <= 0) return BBC_OK;
+    note_launch();
+    const size_t smem = (size_t)tile_words * 4;
+    if (kind == 1)
+        k_tile_motif<1><<<blocks, kTileThreads, smem, st>>>(graph, items, n_items, head, tile_words / 2,
+                                                           tile_words, (uint32_t)k, out);
+    else
+        k_tile_motif<2><<<blocks, kTileThreads, smem, st>>>(graph, items, n_items, head, tile_words,
+                                                           tile_words, (uint32_t)k, out);
+    BBC_CUDA_TRY(cudaGetLastError());
     return BBC_OK;
 }
 

@@ -466,7 +466,8 @@ void release_graph(bbc_graph *g, cudaStream_t st) {
 bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
     if (g->items_valid && g->items_tuning.tile_words == t.tile_words &&
         g->items_tuning.warp_max_wedges == t.warp_max_wedges &&
-        g->items_tuning.split_wedges == t.split_wedges && g->items_tuning.plain == t.plain)
+        g->items_tuning.split_wedges == t.split_wedges && g->items_tuning.plain == t.plain &&
+        g->items_tuning.tiles_only == t.tiles_only)
         return BBC_OK;
     if (g->tile_items) dev_free(g->tile_items, st);
     if (g->warp_items) dev_free(g->warp_items, st);
@@ -505,7 +506,7 @@ bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
     BBC_TRY(sc.get(&nb, (size_t)nS));
     BBC_TRY(dev_alloc_n(&g->boff, (size_t)nS + 1, st));
     ClassifyParams P{g->nS, g->orient_low, t.tile_words, t.warp_max_wedges, t.split_wedges,
-                     t.plain ? 0 : 1};
+                     (t.plain || t.tiles_only) ? 0 : 1};
     note_launch();
     k_classify<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, nt, nh, nb, nw, ng);
     BBC_LAUNCH_CHECK("k_classify");

@@ -68,4 +68,7 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
     assert b"both side flags" in lib.bbc_last_error()
     b = ctypes.c_uint64()
     assert lib.bbc_count(None, ctypes.byref(b), None, None, None, None, None) == 1
+    out = (ctypes.c_uint64 * 6)()
+    assert lib.bbc_count_motif(None, 1, 2, ctypes.addressof(out), None) == 1
+    assert b"bbc_count_motif" in lib.bbc_last_error()
     lib.bbc_graph_free(None)
