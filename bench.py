@@ -226,6 +226,38 @@ def bench_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_motifs(g, u_d, v_d, s_d, W, balanced, unbalanced):
+    """The motif counts on the bench graph (pair side as for the butterfly count): the six
+    sign classes of Table 7 and balanced (2,3)-bicliques. Per kind: one untimed call (it
+    builds the motif work lists), then 3 timed calls; the kernel's device time comes from
+    the library's CUDA events. The classes must add up to the butterfly count's totals."""
+    from paper_2601_17707_gb300 import bbc
+
+    G = bbc.Graph.prepare(g.n_u, g.n_v, u_d, v_d, s_d)
+    out = {}
+    try:
+        peak, _ = hbm_peak()
+        alg_bytes = 4 * W + 20 * g.n_edges        # one wedge pass per call
+        for name, kind, k in (("sign_classes", "classes", 2), ("biclique_2_3", "biclique", 3)):
+            res = G.count_motif(kind, k=k)
+            bbc.profile_start()
+            t0 = time.perf_counter()
+            for _ in range(3):
+                res = G.count_motif(kind, k=k)
+            wall_ms = (time.perf_counter() - t0) * 1e3 / 3
+            prof = bbc.profile_stop()
+            n, ms = prof.get("k_tile_motif", (0, 0.0))
+            kern_ms = ms / max(1, n)
+            out[name] = {"counts": list(res), "kernel_ms": kern_ms, "call_ms": wall_ms,
+                         "wedges_per_s": W / (kern_ms / 1e3) if kern_ms else None,
+                         "roofline_frac": (alg_bytes / (kern_ms / 1e3) / 1e9) / peak if kern_ms else None}
+        cl = out["sign_classes"]["counts"]
+        out["classes_consistent"] = (sum(cl[:4]) == balanced and cl[4] + cl[5] == unbalanced)
+    finally:
+        G.free()
+    return out
+
+
 def bench_batched(args, dev):
     """The batched workload: 4,096 Chung-Lu graphs counted by one replay of a captured CUDA
     graph (autotuned) against per-graph launches of the single-graph path."""
@@ -421,6 +453,10 @@ def bench_gpu(args):
                 "kernel_ms_per_launch": tile_ms / tile_launches,
                 "algorithmic_bytes_per_launch": alg_bytes}
 
+    motifs = None
+    if not args.no_motifs:
+        motifs = bench_motifs(g, u_d, v_d, s_d, W, b_last, int(totals[1].item()))
+
     batched = serving = None
     if not args.no_batched:
         batched, pool = bench_batched(args, dev)
@@ -447,7 +483,7 @@ def bench_gpu(args):
                        "parallelism": f"replicas x{world}", "balanced": b_last},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": launches, "kernel_profile": prof,
-            "batched": batched, "serving": serving,
+            "motifs": motifs, "batched": batched, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -464,6 +500,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-batched", action="store_true", help="skip the 4,096-graph batch")
+    ap.add_argument("--no-motifs", action="store_true", help="skip the sign-class / (2,3) counts")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving sweep")
     ap.add_argument("--serve-rates", type=float, nargs="+",
                     default=[100, 300, 1000, 3000, 10000, 20000])

@@ -89,7 +89,8 @@ struct ProfSlot {
     bool used = false;
 };
 std::vector<ProfSlot> g_prof;
-const char *const kProfNames[kProfKinds] = {"k_tile", "k_warp_hash", "k_warp_tile", "k_group_tile"};
+const char *const kProfNames[kProfKinds] = {"k_tile", "k_warp_hash", "k_warp_tile", "k_group_tile",
+                                            "k_tile_motif"};
 }  // namespace
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }

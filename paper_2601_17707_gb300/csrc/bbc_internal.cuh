@@ -134,7 +134,7 @@ void note_launch();
 // Optional per-kernel timing (bbc_profile_start / bbc_profile_stop): while enabled, the
 // counting kernels are bracketed by CUDA events on their own stream. profile_begin
 // returns a token (-1 when profiling is off or the stream is being captured).
-enum { kProfTile = 0, kProfHash = 1, kProfWarpTile = 2, kProfGroupTile = 3, kProfKinds = 4 };
+enum { kProfTile = 0, kProfHash = 1, kProfWarpTile = 2, kProfGroupTile = 3, kProfMotif = 4, kProfKinds = 5 };
 int profile_begin(int kind, cudaStream_t st);
 bool profiling_active();
 void profile_end(int token, cudaStream_t st);

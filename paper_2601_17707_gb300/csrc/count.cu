@@ -1184,6 +1184,7 @@ bbc_status launch_motif(const DevGraph *graph, const TileItem *items, int n_item
                         cudaStream_t st) {
     BBC_TRY(configure_count_kernels());
     if (n_items <= 0) return BBC_OK;
+    const int tok = profile_begin(kProfMotif, st);
     note_launch();
     const size_t smem = (size_t)tile_words * 4;
     if (kind == 1)
@@ -1193,6 +1194,7 @@ bbc_status launch_motif(const DevGraph *graph, const TileItem *items, int n_item
         k_tile_motif<2><<<blocks, kTileThreads, smem, st>>>(graph, items, n_items, head, tile_words,
                                                            tile_words, (uint32_t)k, out);
     BBC_CUDA_TRY(cudaGetLastError());
+    profile_end(tok, st);
     return BBC_OK;
 }
 
