@@ -254,6 +254,63 @@ bbc_status bbc_server_stats(bbc_server *s, uint64_t *completed, double *p50_us,
 void bbc_server_destroy(bbc_server *s);
 
 /*
+ * Learned cost model of the tile kernel's work items (an extension: the paper orders
+ * Algorithm 4's queue by a fanout estimate, and this library by each item's share of its
+ * anchor's oriented wedges). A small fp32 network (8 item features -> 32 -> 32 -> 1, ReLU)
+ * is trained on the GPU, by this library's own forward, backward and Adam kernels, to
+ * predict an item's duration (standardised log SM cycles) from features the library
+ * computes; bbc_cost_model_order then sorts a graph's tile items by the prediction,
+ * heaviest first. Counts do not depend on the order.
+ *
+ * Parameter layout (fp32, bbc_cost_model_num_params() = 1,377): W1[32][8], b1[32],
+ * W2[32][32] (row j = unit j of the second layer), b2[32], w3[32], b3; the network is
+ * y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3.
+ * Feature rows (8 floats per tile item, in the graph's current queue order): log1p of
+ * the anchor's wedges / 16, log1p(anchor degree) / 16, log1p(tiles in the item) / 8,
+ * log1p(endpoint span of the item) / 16, first tile / the anchor's tiles, counter width
+ * / 2, log1p(|S|) / 16, log1p(wedge share of the item) / 16.
+ */
+typedef struct bbc_cost_model bbc_cost_model;
+
+/* A model with He-uniform weights drawn from SplitMix64(seed) and zero biases. */
+bbc_status bbc_cost_model_create(uint64_t seed, bbc_cost_model **out);
+void bbc_cost_model_free(bbc_cost_model *m);
+int32_t bbc_cost_model_num_params(void);
+/* Host copies of the parameters (capacity >= bbc_cost_model_num_params()). set_params
+   also clears the optimiser state. */
+bbc_status bbc_cost_model_get_params(const bbc_cost_model *m, float *host_out, int32_t capacity);
+bbc_status bbc_cost_model_set_params(bbc_cost_model *m, const float *host_in, int32_t n_params);
+/*
+ * Loss L = (1/n) sum_i (y(x_i) - t_i)^2 and its gradient with respect to every parameter
+ * at the current parameters. X_dev: device float[n][8]; t_dev: device float[n].
+ * loss_host: host float; grad_host: host float[num_params] or NULL. Synchronises.
+ */
+bbc_status bbc_cost_model_loss_grad(bbc_cost_model *m, const float *X_dev, const float *t_dev, int32_t n,
+                                    float *loss_host, float *grad_host, void *cuda_stream);
+/*
+ * Trains on (X_dev, cycles_dev): labels are log(cycles) standardised over the n samples;
+ * `steps` full-batch Adam steps at learning rate lr. loss_host (host float or NULL)
+ * receives the final loss in standardised units. Synchronises.
+ */
+bbc_status bbc_cost_model_fit(bbc_cost_model *m, const float *X_dev, const int64_t *cycles_dev, int32_t n,
+                              int32_t steps, float lr, float *loss_host, void *cuda_stream);
+/* y_dev[i] = the network at X_dev[i] (device float[n]); queued, no synchronisation. */
+bbc_status bbc_cost_model_predict(const bbc_cost_model *m, const float *X_dev, int32_t n, float *y_dev,
+                                  void *cuda_stream);
+/* Feature rows of g's tile items (device float[capacity][8]); *n_items = their number.
+   X_dev = NULL with capacity 0 only reports the number. */
+bbc_status bbc_item_features(bbc_graph *g, float *X_dev, int32_t capacity, int32_t *n_items, void *cuda_stream);
+/*
+ * Runs the tile kernel once over g's tile items (global totals only, the other kernels
+ * are not run) and writes each item's duration in SM cycles (device int64[capacity]),
+ * in queue order. Synchronises.
+ */
+bbc_status bbc_item_cycles(bbc_graph *g, int64_t *cycles_dev, int32_t capacity, int32_t *n_items,
+                           void *cuda_stream);
+/* Sorts g's tile items by the model's prediction, heaviest first. Synchronises. */
+bbc_status bbc_cost_model_order(const bbc_cost_model *m, bbc_graph *g, void *cuda_stream);
+
+/*
  * Accounting for reports (not part of the counting): bbc_launch_count is the number of
  * CUDA kernels this library has launched in this process. Between bbc_profile_start and
  * bbc_profile_stop every launch of a counting kernel (outside stream capture) is

@@ -37,7 +37,10 @@ EXPORTS = (
     "bbc_graph_free", "bbc_count_batch", "bbc_autotune_batch", "bbc_server_create", "bbc_submit",
     "bbc_poll", "bbc_wait", "bbc_server_stats", "bbc_server_destroy", "bbc_status_string",
     "bbc_last_error", "bbc_launch_count", "bbc_profile_start", "bbc_profile_stop",
-    "bbc_count_noalloc", "bbc_count_motif",
+    "bbc_count_noalloc", "bbc_count_motif", "bbc_cost_model_create", "bbc_cost_model_free",
+    "bbc_cost_model_num_params", "bbc_cost_model_get_params", "bbc_cost_model_set_params",
+    "bbc_cost_model_loss_grad", "bbc_cost_model_fit", "bbc_cost_model_predict", "bbc_item_features",
+    "bbc_item_cycles", "bbc_cost_model_order",
 )
 
 MOTIF_SIGN_CLASSES = 1
@@ -111,6 +114,17 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "bbc_last_error": ([], ctypes.c_char_p),
             "bbc_count_noalloc": ([vp, vp, vp], ctypes.c_int),
             "bbc_count_motif": ([vp, i32, i32, vp, vp], ctypes.c_int),
+            "bbc_cost_model_create": ([ctypes.c_uint64, ctypes.POINTER(vp)], ctypes.c_int),
+            "bbc_cost_model_free": ([vp], None),
+            "bbc_cost_model_num_params": ([], i32),
+            "bbc_cost_model_get_params": ([vp, vp, i32], ctypes.c_int),
+            "bbc_cost_model_set_params": ([vp, vp, i32], ctypes.c_int),
+            "bbc_cost_model_loss_grad": ([vp, vp, vp, i32, vp, vp, vp], ctypes.c_int),
+            "bbc_cost_model_fit": ([vp, vp, vp, i32, i32, ctypes.c_float, vp, vp], ctypes.c_int),
+            "bbc_cost_model_predict": ([vp, vp, i32, vp, vp], ctypes.c_int),
+            "bbc_item_features": ([vp, vp, i32, ctypes.POINTER(i32), vp], ctypes.c_int),
+            "bbc_item_cycles": ([vp, vp, i32, ctypes.POINTER(i32), vp], ctypes.c_int),
+            "bbc_cost_model_order": ([vp, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -277,6 +291,38 @@ class Graph:
                                   _stream_ptr(stream)), "bbc_count_motif")
         return tuple(int(x) for x in out[:6 if kind_id == MOTIF_SIGN_CLASSES else 2])
 
+    def item_features(self, stream=None):
+        """Feature rows of the graph's tile items (float32 CUDA tensor [n, 8]), queue order."""
+        import torch
+
+        lib = load()
+        n = ctypes.c_int32()
+        cap = max(1, self._n_tile_items(stream))
+        X = torch.empty((cap, 8), dtype=torch.float32, device="cuda")
+        check(lib.bbc_item_features(self.handle, X.data_ptr(), cap, ctypes.byref(n), _stream_ptr(stream)),
+              "bbc_item_features")
+        return X[: n.value]
+
+    def item_cycles(self, stream=None):
+        """Per tile item, its duration in SM cycles from one instrumented tile-kernel run
+        (int64 CUDA tensor, queue order)."""
+        import torch
+
+        lib = load()
+        n = ctypes.c_int32()
+        cap = max(1, self._n_tile_items(stream))
+        c = torch.empty(cap, dtype=torch.int64, device="cuda")
+        check(lib.bbc_item_cycles(self.handle, c.data_ptr(), cap, ctypes.byref(n), _stream_ptr(stream)),
+              "bbc_item_cycles")
+        return c[: n.value]
+
+    def _n_tile_items(self, stream=None) -> int:
+        lib = load()
+        n = ctypes.c_int32()
+        check(lib.bbc_item_features(self.handle, None, 0, ctypes.byref(n), _stream_ptr(stream)),
+              "bbc_item_features")
+        return n.value
+
     def info(self) -> Info:
         lib = load()
         side = ctypes.c_int32()
@@ -376,5 +422,69 @@ class Server:
     def __del__(self):
         try:
             self.close()
+        except Exception:
+            pass
+
+
+class CostModel:
+    """The learned cost model of the tile kernel's work items (see include/bbc.h)."""
+
+    def __init__(self, seed: int = 0):
+        lib = load()
+        h = ctypes.c_void_p()
+        check(lib.bbc_cost_model_create(int(seed), ctypes.byref(h)), "bbc_cost_model_create")
+        self._h = h
+
+    @staticmethod
+    def num_params() -> int:
+        return int(load().bbc_cost_model_num_params())
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.num_params(), dtype=np.float32)
+        check(load().bbc_cost_model_get_params(self._h, out.ctypes.data, out.shape[0]),
+              "bbc_cost_model_get_params")
+        return out
+
+    def set_params(self, p) -> None:
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        check(load().bbc_cost_model_set_params(self._h, p.ctypes.data, p.shape[0]),
+              "bbc_cost_model_set_params")
+
+    def loss_grad(self, X, t, stream=None):
+        """(loss, gradient as float32 numpy) for device tensors X [n, 8] and t [n]."""
+        loss = ctypes.c_float()
+        g = np.empty(self.num_params(), dtype=np.float32)
+        check(load().bbc_cost_model_loss_grad(self._h, X.data_ptr(), t.data_ptr(), int(X.shape[0]),
+                                              ctypes.byref(loss), g.ctypes.data, _stream_ptr(stream)),
+              "bbc_cost_model_loss_grad")
+        return float(loss.value), g
+
+    def fit(self, X, cycles, steps: int = 300, lr: float = 3e-3, stream=None) -> float:
+        loss = ctypes.c_float()
+        check(load().bbc_cost_model_fit(self._h, X.data_ptr(), cycles.data_ptr(), int(X.shape[0]),
+                                        int(steps), float(lr), ctypes.byref(loss), _stream_ptr(stream)),
+              "bbc_cost_model_fit")
+        return float(loss.value)
+
+    def predict(self, X, stream=None):
+        import torch
+
+        y = torch.empty(max(1, X.shape[0]), dtype=torch.float32, device="cuda")
+        check(load().bbc_cost_model_predict(self._h, X.data_ptr(), int(X.shape[0]), y.data_ptr(),
+                                            _stream_ptr(stream)), "bbc_cost_model_predict")
+        return y[: X.shape[0]]
+
+    def order(self, graph: "Graph", stream=None) -> None:
+        check(load().bbc_cost_model_order(self._h, graph.handle, _stream_ptr(stream)),
+              "bbc_cost_model_order")
+
+    def free(self) -> None:
+        if self._h.value:
+            load().bbc_cost_model_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
         except Exception:
             pass

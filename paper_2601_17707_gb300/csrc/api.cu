@@ -55,6 +55,9 @@ __global__ void k_scatter_per_vertex(const unsigned long long *__restrict__ by_r
         out[perm[r]] = by_rank[r];
 }
 
+}  // namespace
+
+// Fails unless the current device is a usable GB300 (compute capability 10.3).
 bbc_status check_device() {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -74,6 +77,8 @@ bbc_status check_device() {
     }
     return BBC_OK;
 }
+
+namespace {
 
 }  // namespace
 

@@ -151,6 +151,7 @@ bbc_status dev_alloc_n(T **p, size_t n, cudaStream_t st) {
 }
 
 int device_sm_count();
+bbc_status check_device();   // the current device is usable (compute capability 10.3)
 
 // ----------------------------------------------------------------------------- sort/scan
 
@@ -179,6 +180,7 @@ struct CountLaunch {
     int32_t n_gt_items;
     QueueState *queue;          // device, zeroed by the caller before the launch
     Tuning tuning;
+    long long *item_cycles = nullptr;  // device, per tile item: its duration in SM cycles
 };
 
 // One contiguous run of a graph's work items to copy into a combined list, tagged with

@@ -726,7 +726,7 @@ __device__ void run_tile_item(const DevGraph &G, const TileItem &item, int tile_
 // Persistent blocks pop (anchor, tile range) items, heaviest first.
 __global__ void __launch_bounds__(kTileThreads, 2)
 k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, int n_items,
-       unsigned *head, int tile_words, int static_schedule) {
+       unsigned *head, int tile_words, int static_schedule, long long *item_cycles) {
     extern __shared__ uint4 smem_tile[];
     uint32_t *tile = reinterpret_cast<uint32_t *>(smem_tile);
     __shared__ ChunkSmem cs;
@@ -749,6 +749,7 @@ k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, 
         if (it >= n_items) break;
         const TileItem item = items[it];
         const DevGraph &G = graphs[item.graph];
+        const long long t_start = item_cycles ? clock64() : 0;
         unsigned long long bal = 0, unb = 0;
         switch (tile_width_of(item)) {
             case 0: run_tile_item<0>(G, item, tile_words, tile, cs, bal, unb); break;
@@ -771,6 +772,8 @@ k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, 
             if (B) red_add(G.totals + 0, B);
             if (U) red_add(G.totals + 1, U);
             if (G.bS && B) red_add(G.bS + item.anchor, B);
+            // the item's duration on this SM (cost-model labels; off when NULL)
+            if (item_cycles) item_cycles[it] = clock64() - t_start;
         }
     }
 }
@@ -1144,7 +1147,8 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
         // schedule: one block per item
         const int grid = T.plain ? L.n_tile_items : std::min(L.n_tile_items, sms * T.blocks_per_sm);
         k_tile<<<grid, kTileThreads, (size_t)T.tile_words * 4, st>>>(
-            L.graphs, L.tile_items, L.n_tile_items, &L.queue->tile_head, T.tile_words, T.plain);
+            L.graphs, L.tile_items, L.n_tile_items, &L.queue->tile_head, T.tile_words, T.plain,
+            L.item_cycles);
         BBC_CUDA_TRY(cudaGetLastError());
         profile_end(tok, st);
     }
@@ -1204,7 +1208,7 @@ bbc_status launch_tile_only(const DevGraph *graphs, const TileItem *items, int n
     if (n_items <= 0) return BBC_OK;
     note_launch();
     k_tile<<<blocks, kTileThreads, (size_t)tile_words * 4, st>>>(graphs, items, n_items, head,
-                                                                 tile_words, 0);
+                                                                 tile_words, 0, nullptr);
     BBC_CUDA_TRY(cudaGetLastError());
     return BBC_OK;
 }

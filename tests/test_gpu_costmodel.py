@@ -1,0 +1,141 @@
+"""GPU tests of the learned cost model: the forward pass and the gradient of the library's
+own kernels against the float64 oracle, training on measured item durations, and what the
+trained network gains over the wedge-share order of the work queue on graphs it was not
+trained on.
+"""
+
+from __future__ import annotations
+
+import heapq
+
+import numpy as np
+import pytest
+
+from oracle import costmodel as cm
+from paper_2601_17707_gb300 import bbc, synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _away_from_kinks(p, X, margin=1e-3):
+    """Rows whose hidden pre-activations all sit farther than `margin` from 0, so that
+    float32 and float64 take the same ReLU branches."""
+    _, (_, z1, _, z2, _, _) = cm.forward(p, X)
+    return (np.abs(z1).min(axis=1) > margin) & (np.abs(z2).min(axis=1) > margin)
+
+
+def test_forward_and_gradient_match_the_oracle(gpu_lib):
+    rng = np.random.default_rng(0)
+    p = rng.normal(0, 0.3, cm.N_PARAMS).astype(np.float32)
+    X = rng.uniform(0, 1.5, (6000, cm.KF)).astype(np.float32)
+    X = X[_away_from_kinks(p.astype(np.float64), X.astype(np.float64))][:4096]
+    t = rng.normal(0, 1, X.shape[0]).astype(np.float32)
+    m = bbc.CostModel(seed=1)
+    m.set_params(p)
+    Xd, td = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
+    # fp32 sums of at most 33 products per unit: 1e-4 relative is a wide margin
+    y = m.predict(Xd).cpu().numpy()
+    y_ref, _ = cm.forward(p.astype(np.float64), X.astype(np.float64))
+    assert np.allclose(y, y_ref, rtol=1e-4, atol=1e-4 * np.abs(y_ref).max())
+    L, g = m.loss_grad(Xd, td)
+    L_ref, g_ref = cm.grad(p.astype(np.float64), X.astype(np.float64), t.astype(np.float64))
+    assert L == pytest.approx(L_ref, rel=1e-4)
+    # per-sample gradients summed over 4,096 samples in fp32 (per-lane sums, then atomics)
+    scale = np.abs(g_ref).max()
+    assert np.abs(g.astype(np.float64) - g_ref).max() <= 2e-4 * scale
+    # the parameters round-trip
+    assert np.array_equal(m.get_params(), p)
+
+
+def _items(g):
+    G = bbc.Graph.from_synthetic(g)
+    X = G.item_features()
+    c = G.item_cycles()
+    return G, X, c
+
+
+def test_training_reduces_the_loss(gpu_lib):
+    G, X, c = _items(synth.powerlaw_1m_200k(seed=11, scale=0.1))
+    try:
+        assert X.shape[0] == c.shape[0] > 1000
+        assert bool((c > 0).all())
+        m = bbc.CostModel(seed=0)
+        start = m.fit(X, c, steps=0)
+        end = m.fit(X, c, steps=500, lr=3e-3)
+        assert end < 0.5 * start and end < 0.5      # standardised labels: variance 1
+    finally:
+        G.free()
+
+
+def _spearman(a, b):
+    ra = np.argsort(np.argsort(a)).astype(np.float64)
+    rb = np.argsort(np.argsort(b)).astype(np.float64)
+    return float(np.corrcoef(ra, rb)[0, 1])
+
+
+def _makespan(order, cost, workers):
+    """Greedy list schedule, items in `order` to the first free worker: what the
+    persistent queue does."""
+    heap = [0.0] * workers
+    for i in order:
+        heapq.heapreplace(heap, heap[0] + float(cost[i]))
+    return max(heap)
+
+
+def test_what_the_learned_model_gains_over_the_wedge_estimate(gpu_lib):
+    """Trained on the item durations of five graphs, evaluated on a sixth. The queue's
+    own estimate of an item's cost is its share of the anchor's wedges (feature 7). The
+    network's gain is in predicting the cost itself: its held-out error in log cycles is
+    compared with the best affine map of the wedge share (least squares on the same
+    training items). Ordering the queue by either gives the same makespan here (the
+    wedge share already ranks items almost perfectly, and even the true costs leave
+    under 1 % to gain), which the test reports and bounds."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    Xs, cs = [], []
+    for seed, scale in ((21, 0.05), (22, 0.08), (23, 0.12), (24, 0.15)):
+        G, X, c = _items(synth.powerlaw_1m_200k(seed=seed, scale=scale))
+        Xs.append(X)
+        cs.append(c)
+        G.free()
+    G, X, c = _items(synth.hubs_50k_2m(seed=5, scale=0.01))
+    Xs.append(X)
+    cs.append(c)
+    G.free()
+    X_train, c_train = torch.cat(Xs), torch.cat(cs)
+    m = bbc.CostModel(seed=0)
+    m.fit(X_train, c_train, steps=800, lr=3e-3)
+    log_train = np.log(np.maximum(c_train.cpu().numpy(), 1).astype(np.float64))
+    mu, sd = log_train.mean(), log_train.std()
+    share_train = X_train[:, 7].cpu().numpy().astype(np.float64)
+    A = np.stack([share_train, np.ones_like(share_train)], axis=1)
+    coef, *_ = np.linalg.lstsq(A, log_train, rcond=None)
+
+    g = synth.powerlaw_1m_200k(seed=31, scale=0.1)          # not seen in training
+    G, X, c = _items(g)
+    try:
+        cost = c.cpu().numpy().astype(np.float64)
+        log_test = np.log(np.maximum(cost, 1))
+        pred = m.predict(X).cpu().numpy().astype(np.float64) * sd + mu    # log cycles
+        share = X[:, 7].cpu().numpy().astype(np.float64)
+        lin = coef[0] * share + coef[1]
+        mse_model = float(np.mean((pred - log_test) ** 2))
+        mse_share = float(np.mean((lin - log_test) ** 2))
+        rho_model, rho_share = _spearman(pred, cost), _spearman(share, cost)
+        workers = 2 * sms
+        ms_share = _makespan(np.argsort(-share, kind="stable"), cost, workers)
+        ms_model = _makespan(np.argsort(-pred, kind="stable"), cost, workers)
+        ms_best = _makespan(np.argsort(-cost, kind="stable"), cost, workers)
+        print(f"held-out log-cycle MSE: network {mse_model:.4f}, affine wedge share {mse_share:.4f}; "
+              f"rank correlation: network {rho_model:.3f}, wedge share {rho_share:.3f}; "
+              f"simulated makespan (cycles): wedge order {ms_share:.4g}, learned {ms_model:.4g}, "
+              f"true-cost order {ms_best:.4g}")
+        assert mse_model < mse_share
+        assert rho_model > rho_share - 0.02
+        assert ms_model <= 1.02 * ms_share
+        # the real queue with the learned order: same counts
+        before = G.count()[:2]
+        m.order(G)
+        assert G.count()[:2] == before
+    finally:
+        G.free()
