@@ -254,6 +254,26 @@ bbc_status bbc_server_stats(bbc_server *s, uint64_t *completed, double *p50_us,
 void bbc_server_destroy(bbc_server *s);
 
 /*
+ * bbc_count_delta -- the exact change of the counts when a batch of edge updates is
+ * applied to a prepared graph (dynamic signed graphs, named as future work in Sec. VIII;
+ * this library's extension). Update i sets the sign of edge (u[i], v[i]) to new_sign[i]:
+ * +1 or -1 inserts the edge or re-signs it, 0 deletes it. The graph itself is not changed.
+ *
+ *   d_balanced    host int64: B(G') - B(G), balanced butterflies (Def. 2). Required.
+ *   d_unbalanced  host int64 or NULL: the same for unbalanced butterflies.
+ *   flags         BBC_INPUT_DEVICE when u, v, new_sign are device pointers.
+ * Only pairs {a, w} of the pair side with a member touched by an update can change
+ * (Lemma 1 counts per pair); each such pair is recounted before and after the batch,
+ * so the work is the 2-hop neighbourhood of the touched pair-side vertices.
+ * Errors: BBC_E_OUT_OF_RANGE (an id), BBC_E_BAD_SIGN (a sign other than -1, 0, +1),
+ * BBC_E_DUPLICATE_EDGE (one pair twice in the batch), BBC_E_INVALID_ARG (deleting an
+ * absent edge, NULL arguments). Synchronises `cuda_stream`.
+ */
+bbc_status bbc_count_delta(const bbc_graph *g, int64_t n_updates, const int32_t *u, const int32_t *v,
+                           const int8_t *new_sign, uint32_t flags, int64_t *d_balanced,
+                           int64_t *d_unbalanced, void *cuda_stream);
+
+/*
  * Learned cost model of the tile kernel's work items (an extension: the paper orders
  * Algorithm 4's queue by a fanout estimate, and this library by each item's share of its
  * anchor's oriented wedges). A small fp32 network (8 item features -> 32 -> 32 -> 1, ReLU)

@@ -18,6 +18,9 @@ Contents:
 * ``brute_force_classes`` / ``brute_force_bicliques``: those two taken literally, by
   enumerating 4-tuples (classified by the two centres' sign patterns) and every k-subset
   of a pair's common neighbours (checked for an unbalanced butterfly). Tiny graphs only.
+* ``apply_updates`` / ``count_delta``: a batch of edge updates applied to the edge list
+  (sign +1 / -1 sets the edge, 0 deletes it) and the change of both counts, by counting
+  the graph before and after with ``count``.
 * ``matrix_counts``: the signed/unsigned co-occurrence identity with a library
   matmul (numpy float64 BLAS; exact, since every product and partial sum is an
   integer of magnitude at most |V| < 2^53, then converted to int64). For the signed biadjacency A (entries +1, -1, 0) and
@@ -222,6 +225,44 @@ def brute_force_bicliques(g, k: int, side: int = 0) -> tuple:
                    for x, y in itertools.combinations(sub, 2)):
                 bal += 1
     return bal, total
+
+
+@dataclass
+class EdgeList:
+    n_u: int
+    n_v: int
+    u: np.ndarray
+    v: np.ndarray
+    sign: np.ndarray
+
+
+def apply_updates(g, u, v, new_sign) -> EdgeList:
+    """The graph after setting edge (u[i], v[i]) to new_sign[i] (0 deletes it). Raises on a
+    pair repeated in the batch or a deletion of an absent edge."""
+    edges = {(a, b): s for a, b, s in zip(np.asarray(g.u).tolist(), np.asarray(g.v).tolist(),
+                                          np.asarray(g.sign).tolist())}
+    seen = set()
+    for a, b, s in zip(np.asarray(u).tolist(), np.asarray(v).tolist(), np.asarray(new_sign).tolist()):
+        if (a, b) in seen:
+            raise ValueError("update batch repeats an edge")
+        seen.add((a, b))
+        if s == 0:
+            if (a, b) not in edges:
+                raise ValueError("deletion of an absent edge")
+            del edges[(a, b)]
+        else:
+            edges[(a, b)] = s
+    keys = sorted(edges)
+    return EdgeList(g.n_u, g.n_v, np.array([k[0] for k in keys], dtype=np.int32),
+                    np.array([k[1] for k in keys], dtype=np.int32),
+                    np.array([edges[k] for k in keys], dtype=np.int8))
+
+
+def count_delta(g, u, v, new_sign, threads: int = 1) -> tuple:
+    """(B(G') - B(G), Ub(G') - Ub(G)) for the batch, by two full counts."""
+    before = count(g, threads=threads, per_vertex=False)
+    after = count(apply_updates(g, u, v, new_sign), threads=threads, per_vertex=False)
+    return after.balanced - before.balanced, after.unbalanced - before.unbalanced
 
 
 def brute_force(g) -> Counts:

@@ -40,7 +40,7 @@ EXPORTS = (
     "bbc_count_noalloc", "bbc_count_motif", "bbc_cost_model_create", "bbc_cost_model_free",
     "bbc_cost_model_num_params", "bbc_cost_model_get_params", "bbc_cost_model_set_params",
     "bbc_cost_model_loss_grad", "bbc_cost_model_fit", "bbc_cost_model_predict", "bbc_item_features",
-    "bbc_item_cycles", "bbc_cost_model_order",
+    "bbc_item_cycles", "bbc_cost_model_order", "bbc_count_delta",
 )
 
 MOTIF_SIGN_CLASSES = 1
@@ -125,6 +125,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "bbc_item_features": ([vp, vp, i32, ctypes.POINTER(i32), vp], ctypes.c_int),
             "bbc_item_cycles": ([vp, vp, i32, ctypes.POINTER(i32), vp], ctypes.c_int),
             "bbc_cost_model_order": ([vp, vp, vp], ctypes.c_int),
+            "bbc_count_delta": ([vp, i64, vp, vp, vp, u32, ctypes.POINTER(i64), ctypes.POINTER(i64), vp],
+                                ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -290,6 +292,19 @@ class Graph:
         check(lib.bbc_count_motif(self.handle, kind_id, int(k), ctypes.addressof(out),
                                   _stream_ptr(stream)), "bbc_count_motif")
         return tuple(int(x) for x in out[:6 if kind_id == MOTIF_SIGN_CLASSES else 2])
+
+    def count_delta(self, u, v, new_sign, stream=None) -> tuple:
+        """(change in balanced, change in unbalanced butterflies) if edge (u[i], v[i]) took
+        sign new_sign[i] (+1 / -1; 0 deletes). The graph is not modified."""
+        lib = load()
+        pu, pv, ps, n, on_dev, keep = _edge_arrays(u, v, new_sign)
+        db = ctypes.c_int64()
+        dub = ctypes.c_int64()
+        check(lib.bbc_count_delta(self.handle, n, pu, pv, ps, INPUT_DEVICE if on_dev else 0,
+                                  ctypes.byref(db), ctypes.byref(dub), _stream_ptr(stream)),
+              "bbc_count_delta")
+        del keep
+        return int(db.value), int(dub.value)
 
     def item_features(self, stream=None):
         """Feature rows of the graph's tile items (float32 CUDA tensor [n, 8]), queue order."""
