@@ -258,6 +258,73 @@ def bench_motifs(g, u_d, v_d, s_d, W, balanced, unbalanced):
     return out
 
 
+def bench_dynamic_batch(g, n_updates, seed):
+    """A batch of edge updates on the bench graph (a third each: sign flips and deletions
+    of present edges, insertions of absent pairs): bbc_count_delta's time against
+    re-preparing and recounting the updated graph, and the two results compared."""
+    import torch
+
+    from paper_2601_17707_gb300 import bbc
+
+    rng = np.random.default_rng(seed)
+    keys = g.u.astype(np.int64) * g.n_v + g.v.astype(np.int64)      # sorted, distinct
+    k3 = n_updates // 3
+    pick = rng.choice(keys.shape[0], size=2 * k3, replace=False)
+    flip, dele = pick[:k3], pick[k3:]
+    ins = []
+    while len(ins) < n_updates - 2 * k3:
+        cand = int(rng.integers(0, g.n_u)) * g.n_v + int(rng.integers(0, g.n_v))
+        j = np.searchsorted(keys, cand)
+        if (j >= keys.shape[0] or keys[j] != cand) and cand not in ins:
+            ins.append(cand)
+    ins = np.array(ins, dtype=np.int64)
+    uk = np.concatenate([keys[flip], keys[dele], ins])
+    u = (uk // g.n_v).astype(np.int32)
+    v = (uk % g.n_v).astype(np.int32)
+    s = np.concatenate([-g.sign[flip], np.zeros(k3, np.int8),
+                        np.where(rng.random(ins.shape[0]) < 0.8, 1, -1)]).astype(np.int8)
+    # the updated edge list
+    keep = np.ones(keys.shape[0], dtype=bool)
+    keep[dele] = False
+    sign2 = g.sign.copy()
+    sign2[flip] = -sign2[flip]
+    u2 = np.concatenate([g.u[keep], (ins // g.n_v).astype(np.int32)])
+    v2 = np.concatenate([g.v[keep], (ins % g.n_v).astype(np.int32)])
+    s2 = np.concatenate([sign2[keep], s[2 * k3:]]).astype(np.int8)
+    dev = torch.device("cuda")
+    u_d, v_d, s_d = (torch.from_numpy(x).to(dev) for x in (u, v, s))
+    G = bbc.Graph.prepare(g.n_u, g.n_v, torch.from_numpy(g.u).to(dev), torch.from_numpy(g.v).to(dev),
+                          torch.from_numpy(g.sign).to(dev))
+    try:
+        b0, ub0 = G.count()[:2]
+        G.count_delta(u_d, v_d, s_d)
+        times = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            d = G.count_delta(u_d, v_d, s_d)
+            times.append((time.perf_counter() - t0) * 1e3)
+    finally:
+        G.free()
+    u2d, v2d, s2d = (torch.from_numpy(x).to(dev) for x in (u2, v2, s2))
+    recount = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G2 = bbc.Graph.prepare(g.n_u, g.n_v, u2d, v2d, s2d)
+        b1, ub1 = G2.count()[:2]
+        recount.append((time.perf_counter() - t0) * 1e3)
+        G2.free()
+    return {"updates": int(n_updates), "delta_ms": float(np.median(times)),
+            "prepare_and_count_ms": float(np.median(recount)),
+            "delta": list(d), "exact": (b1 - b0, ub1 - ub0) == tuple(d),
+            "timing": "host wall clock around each call (both synchronise), median"}
+
+
+def bench_dynamic(g, sizes=(10, 100, 1000)):
+    return [bench_dynamic_batch(g, n, seed=7 + i) for i, n in enumerate(sizes)]
+
+
 def bench_batched(args, dev):
     """The batched workload: 4,096 Chung-Lu graphs counted by one replay of a captured CUDA
     graph (autotuned) against per-graph launches of the single-graph path."""
@@ -453,9 +520,10 @@ def bench_gpu(args):
                 "kernel_ms_per_launch": tile_ms / tile_launches,
                 "algorithmic_bytes_per_launch": alg_bytes}
 
-    motifs = None
+    motifs = dynamic = None
     if not args.no_motifs:
         motifs = bench_motifs(g, u_d, v_d, s_d, W, b_last, int(totals[1].item()))
+        dynamic = bench_dynamic(g)
 
     batched = serving = None
     if not args.no_batched:
@@ -483,7 +551,7 @@ def bench_gpu(args):
                        "parallelism": f"replicas x{world}", "balanced": b_last},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": launches, "kernel_profile": prof,
-            "motifs": motifs, "batched": batched, "serving": serving,
+            "motifs": motifs, "dynamic": dynamic, "batched": batched, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -500,7 +568,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-batched", action="store_true", help="skip the 4,096-graph batch")
-    ap.add_argument("--no-motifs", action="store_true", help="skip the sign-class / (2,3) counts")
+    ap.add_argument("--no-motifs", action="store_true",
+                    help="skip the sign-class / (2,3) counts and the update-batch delta")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving sweep")
     ap.add_argument("--serve-rates", type=float, nargs="+",
                     default=[100, 300, 1000, 3000, 10000, 20000])

@@ -14,7 +14,9 @@
 // Steps: ids -> ranks (k_rank_of); updates -> (a, c, old sign from the CSR, new sign)
 // with range and sign checks (k_map_updates); stable radix sorts by a and by (c, a);
 // duplicate and absent-deletion checks (k_check_updates); the distinct anchors A
-// (k_anchor_marks + scan); one block per anchor of A (k_delta_anchor).
+// (k_anchor_marks + scan); one block per anchor of A (k_delta_anchor), which adds into
+// four global counters per endpoint (short centre rows a warp each, long ones the whole
+// block) and then reads and clears the whole counter array.
 #include "graph.cuh"
 
 namespace bbc {
@@ -160,29 +162,26 @@ struct DeltaArgs {
     const uint32_t *anchors, *seg_begin;
     int32_t n_anchors;
     const uint8_t *in_a;
-    // per block scratch: 4 counters (old p, old n, new p, new n) and a touch flag per
-    // endpoint, and a touched list
+    // per block scratch: 4 counters (old p, old n, new p, new n) per endpoint, zero
+    // between anchors
     uint32_t *cnt;
-    uint32_t *flag;
-    uint32_t *touched;
     unsigned *next_anchor;
     unsigned long long *out;   // [0] delta balanced, [1] delta unbalanced (two's complement)
 };
 
-__device__ __forceinline__ void touch(const DeltaArgs &A, uint32_t *cnt, uint32_t *flag, uint32_t *touched,
-                                      unsigned *s_nt, uint32_t w, int slot) {
-    if (atomicExch(flag + w, 1u) == 0u) touched[atomicAdd(s_nt, 1u)] = w;
+__device__ __forceinline__ void touch(uint32_t *cnt, uint32_t w, int slot) {
     atomicAdd(cnt + 4 * (size_t)w + slot, 1u);
 }
 
 // One centre c of anchor a: its old row, with every entry's new sign looked up among the
-// updates, then the insertions at c.
+// updates, then the insertions at c. Threads t, t + step, ... of the caller's group share
+// the row.
 __device__ void delta_centre(const DeltaArgs &A, uint32_t a, uint32_t c, uint32_t oa, uint32_t na,
-                             uint32_t *cnt, uint32_t *flag, uint32_t *touched, unsigned *s_nt, int lane) {
+                             uint32_t *cnt, int t, int step) {
     const int64_t b = A.rowC_off[c], e = A.rowC_off[c + 1];
     const int64_t u0 = lower_key(A.key, A.n_upd, (unsigned long long)c << 32);
     const int64_t u1 = lower_key(A.key, A.n_upd, ((unsigned long long)c + 1) << 32);
-    for (int64_t j = b + lane; j < e; j += 32) {
+    for (int64_t j = b + t; j < e; j += step) {
         const uint32_t x = A.rowC[j];
         const uint32_t w = x & kIdMask;
         if (w == a) continue;
@@ -200,66 +199,81 @@ __device__ void delta_centre(const DeltaArgs &A, uint32_t a, uint32_t c, uint32_
             }
             if (lo < u1 && A.key[lo] == k) nw = A.knew[lo];
         }
-        if (oa && ow) touch(A, cnt, flag, touched, s_nt, w, oa == ow ? 0 : 1);
-        if (na && nw) touch(A, cnt, flag, touched, s_nt, w, na == nw ? 2 : 3);
+        if (oa && ow) touch(cnt, w, oa == ow ? 0 : 1);
+        if (na && nw) touch(cnt, w, na == nw ? 2 : 3);
     }
     if (na)
-        for (int64_t q = u0 + lane; q < u1; q += 32) {
+        for (int64_t q = u0 + t; q < u1; q += step) {
             if (A.kold[q] != kAbsent || A.knew[q] == kAbsent) continue;   // insertions only
             const uint32_t w = (uint32_t)(A.key[q] & 0xffffffffull);
             if (w == a) continue;
-            touch(A, cnt, flag, touched, s_nt, w, na == A.knew[q] ? 2 : 3);
+            touch(cnt, w, na == A.knew[q] ? 2 : 3);
         }
 }
 
+// The new sign code of edge (a, c) given its old one.
+__device__ __forceinline__ uint32_t new_code(const DeltaArgs &A, uint32_t a, uint32_t c, uint32_t oa) {
+    const unsigned long long k = ((unsigned long long)c << 32) | a;
+    const int64_t q = lower_key(A.key, A.n_upd, k);
+    return (q < A.n_upd && A.key[q] == k) ? A.knew[q] : oa;
+}
+
+constexpr int64_t kLongRow = 1024;   // centre rows this long are swept by the whole block
+
 __global__ void __launch_bounds__(kDeltaThreads) k_delta_anchor(DeltaArgs A) {
-    __shared__ unsigned s_nt;
     __shared__ int s_item;
     __shared__ long long s_red[2][kDeltaWarps];
     uint32_t *cnt = A.cnt + (size_t)blockIdx.x * 4 * (size_t)A.nS;
-    uint32_t *flag = A.flag + (size_t)blockIdx.x * (size_t)A.nS;
-    uint32_t *touched = A.touched + (size_t)blockIdx.x * (size_t)A.nS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     long long db = 0, du = 0;
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_item = (int)atomicAdd(A.next_anchor, 1u);
-            s_nt = 0;
-        }
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(A.next_anchor, 1u);
         __syncthreads();
         const int it = s_item;
         if (it >= A.n_anchors) break;
         const uint32_t a = A.anchors[it];
         const uint32_t sb = A.seg_begin[it];
         const uint32_t se = it + 1 < A.n_anchors ? A.seg_begin[it + 1] : (uint32_t)A.n_upd;
-        // old centres of a (re-signed or deleted ones through the update list)
         const int64_t rb = A.rowS_off[a], re = A.rowS_off[a + 1];
+        // short centre rows: a warp each
         for (int64_t i = rb + warp; i < re; i += kDeltaWarps) {
             const uint32_t x = A.rowS[i];
             const uint32_t c = x & kIdMask;
+            if (A.rowC_off[c + 1] - A.rowC_off[c] >= kLongRow) continue;
             const uint32_t oa = (x >> 31) ? 2u : 1u;
-            uint32_t na = oa;
-            const unsigned long long k = ((unsigned long long)c << 32) | a;
-            const int64_t q = lower_key(A.key, A.n_upd, k);
-            if (q < A.n_upd && A.key[q] == k) na = A.knew[q];   // (a, c) re-signed or deleted
-            delta_centre(A, a, c, oa, na, cnt, flag, touched, &s_nt, lane);
+            delta_centre(A, a, c, oa, new_code(A, a, c, oa), cnt, lane, 32);
         }
-        // new centres of a
-        for (uint32_t q = sb + warp; q < se; q += kDeltaWarps)
-            if (A.old_by_a[q] == kAbsent && A.new_by_a[q] != kAbsent)
-                delta_centre(A, a, A.c_by_a[q], kAbsent, A.new_by_a[q], cnt, flag, touched, &s_nt, lane);
+        for (uint32_t q = sb + warp; q < se; q += kDeltaWarps) {
+            const uint32_t c = A.c_by_a[q];
+            if (A.old_by_a[q] == kAbsent && A.new_by_a[q] != kAbsent &&
+                A.rowC_off[c + 1] - A.rowC_off[c] < kLongRow)
+                delta_centre(A, a, c, kAbsent, A.new_by_a[q], cnt, lane, 32);
+        }
+        // long centre rows: the whole block each
+        for (int64_t i = rb; i < re; ++i) {
+            const uint32_t x = A.rowS[i];
+            const uint32_t c = x & kIdMask;
+            if (A.rowC_off[c + 1] - A.rowC_off[c] < kLongRow) continue;
+            const uint32_t oa = (x >> 31) ? 2u : 1u;
+            delta_centre(A, a, c, oa, new_code(A, a, c, oa), cnt, threadIdx.x, kDeltaThreads);
+        }
+        for (uint32_t q = sb; q < se; ++q) {
+            const uint32_t c = A.c_by_a[q];
+            if (A.old_by_a[q] == kAbsent && A.new_by_a[q] != kAbsent &&
+                A.rowC_off[c + 1] - A.rowC_off[c] >= kLongRow)
+                delta_centre(A, a, c, kAbsent, A.new_by_a[q], cnt, threadIdx.x, kDeltaThreads);
+        }
         __syncthreads();
-        const unsigned nt = s_nt;
-        for (unsigned i = threadIdx.x; i < nt; i += blockDim.x) {
-            const uint32_t w = touched[i];
-            uint32_t *k4 = cnt + 4 * (size_t)w;
-            const long long po = k4[0], no = k4[1], pn = k4[2], nn = k4[3];
-            if (!A.in_a[w] || w > a) {
-                db += (pn * (pn - 1) / 2 + nn * (nn - 1) / 2) - (po * (po - 1) / 2 + no * (no - 1) / 2);
-                du += pn * nn - po * no;
-            }
-            k4[0] = k4[1] = k4[2] = k4[3] = 0;
-            flag[w] = 0;
+        // every endpoint's four counters, read 16 bytes at a time, then cleared
+        uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
+        for (int64_t w = threadIdx.x; w < A.nS; w += kDeltaThreads) {
+            const uint4 k4 = c4[w];
+            if ((k4.x | k4.y | k4.z | k4.w) == 0) continue;
+            c4[w] = make_uint4(0u, 0u, 0u, 0u);
+            if (A.in_a[w] && (uint32_t)w < a) continue;   // the pair is counted at w
+            const long long po = k4.x, no = k4.y, pn = k4.z, nn = k4.w;
+            db += (pn * (pn - 1) / 2 + nn * (nn - 1) / 2) - (po * (po - 1) / 2 + no * (no - 1) / 2);
+            du += pn * nn - po * no;
         }
         __syncthreads();
     }
@@ -453,19 +467,16 @@ extern "C" bbc_status bbc_count_delta(const bbc_graph *g, int64_t n_updates, con
             set_error("bbc_count_delta: a deletion of an edge the graph does not hold");
             return BBC_E_INVALID_ARG;
         }
-        // per-block scratch: 24 bytes per pair-side vertex, at most ~4 GB in all
-        const int64_t per_block = 24 * std::max<int64_t>(nS, 1);
+        // per-block scratch: 16 bytes per pair-side vertex, at most ~4 GB in all
+        const int64_t per_block = 16 * std::max<int64_t>(nS, 1);
         int64_t blocks = std::min<int64_t>(n_anchors, (int64_t)device_sm_count() * 2);
         blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, ((int64_t)4 << 30) / per_block));
-        uint32_t *cnt = nullptr, *flag = nullptr, *touched = nullptr;
+        uint32_t *cnt = nullptr;
         BBC_TRY(B.get(&cnt, (size_t)blocks * 4 * (size_t)std::max<int64_t>(nS, 1)));
-        BBC_TRY(B.get(&flag, (size_t)blocks * (size_t)std::max<int64_t>(nS, 1)));
-        BBC_TRY(B.get(&touched, (size_t)blocks * (size_t)std::max<int64_t>(nS, 1)));
         BBC_CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)blocks * 16 * (size_t)std::max<int64_t>(nS, 1), st));
-        BBC_CUDA_TRY(cudaMemsetAsync(flag, 0, (size_t)blocks * 4 * (size_t)std::max<int64_t>(nS, 1), st));
         DeltaArgs A{g->rowS_off, g->rowS, g->rowC_off, g->rowC, nS, key, kold, knew, n,
                     k1, c_by_a, old_by_a, new_by_a, anchors, seg, (int32_t)n_anchors, in_a,
-                    cnt, flag, touched, next, out};
+                    cnt, next, out};
         note_launch();
         k_delta_anchor<<<(unsigned)blocks, kDeltaThreads, 0, st>>>(A);
         BBC_CUDA_TRY(cudaGetLastError());
