@@ -325,6 +325,22 @@ def bench_dynamic(g, sizes=(10, 100, 1000)):
     return [bench_dynamic_batch(g, n, seed=7 + i) for i, n in enumerate(sizes)]
 
 
+def per_kernel_roofline(work, prof, passes, peak):
+    """{kernel: achieved GB/s and fraction of `peak`} from the work behind each path
+    (wedges and pair-side edges of its anchors; 4 B per wedge visit, `passes` visits per
+    wedge, 20 B per edge) and its CUDA-event time per launch."""
+    out = {}
+    for k, (items, wedges, edges) in work.items():
+        n, ms = prof.get(k, (0, 0.0))
+        if not n or not items:
+            continue
+        alg = 4 * passes * wedges + 20 * edges
+        gbs = alg / (ms / n / 1e3) / 1e9
+        out[k] = {"items": items, "wedges": wedges, "ms_per_launch": ms / n,
+                  "algorithmic_bytes": alg, "achieved_gbs": gbs, "frac": gbs / peak}
+    return out
+
+
 def bench_batched(args, dev):
     """The batched workload: 4,096 Chung-Lu graphs counted by one replay of a captured CUDA
     graph (autotuned) against per-graph launches of the single-graph path."""
@@ -351,6 +367,19 @@ def bench_batched(args, dev):
         got = bbc.count_batch(G)
     t_batch = (time.perf_counter() - t0) / reps
     exact = got == ref
+    # per-kernel device times of one batch (launched directly while profiling) and the
+    # work behind each path, from the tuned lists the plan used
+    bbc.profile_start()
+    bbc.count_batch(G)
+    prof = bbc.profile_stop()
+    work = {}
+    for h in G:
+        for k, t in h.work().items():
+            a = work.setdefault(k, [0, 0, 0])
+            for i in range(3):
+                a[i] += t[i]
+    peak, _ = hbm_peak()
+    kernels = per_kernel_roofline({k: tuple(v) for k, v in work.items()}, prof, 1, peak)
     # per-graph launches on one stream with one sync at the end: the plain kernel
     # (static one-block-per-anchor schedule) and, for context, the work-queue kernel
     totals = torch.empty(2 * len(G), dtype=torch.int64, device=dev)
@@ -383,7 +412,7 @@ def bench_batched(args, dev):
             "speedup_vs_per_graph_plain": t_per / t_batch,
             "per_graph_queue_graphs_per_s": len(G) / t_per_q, "per_graph_queue_ms": 1e3 * t_per_q,
             "speedup_vs_per_graph_queue": t_per_q / t_batch,
-            "counts_identical": bool(exact), "tuning": tuned.as_dict(),
+            "counts_identical": bool(exact), "tuning": tuned.as_dict(), "kernels": kernels,
             "timing": f"host wall clock around bbc_count_batch (replay + D2H + sync), mean of "
                       f"{reps}; per-graph: bbc_count_async per graph on one stream, one sync "
                       "(plain = static one-block-per-anchor kernel; queue = work-queue kernel)",
@@ -454,6 +483,7 @@ def bench_gpu(args):
 
     G0 = bbc.Graph.prepare(g.n_u, g.n_v, u_d, v_d, s_d)
     info = G0.info()
+    work0 = G0.work()
     G0.free()
     W = info.wedges
 
@@ -551,6 +581,7 @@ def bench_gpu(args):
                        "parallelism": f"replicas x{world}", "balanced": b_last},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": launches, "kernel_profile": prof,
+            "kernels": per_kernel_roofline(work0, prof, 2, hbm_peak()[0]),
             "motifs": motifs, "dynamic": dynamic, "batched": batched, "serving": serving,
         }
         print(json.dumps(line), flush=True)

@@ -155,6 +155,14 @@ bbc_status bbc_count_async(bbc_graph *g, uint64_t *totals_dev, uint64_t *per_u,
  */
 bbc_status bbc_count_noalloc(const bbc_graph *g, uint64_t *totals_dev, void *cuda_stream);
 
+/*
+ * bbc_graph_work -- the work behind a prepared graph's current work lists (built with the
+ * default tuning if it has none), for per-kernel reports: out (host uint64[12]) holds, for
+ * the block-tile, group-tile, warp-tile and hash paths in that order, {work items, oriented
+ * wedges of their anchors, pair-side edges of their anchors}. Synchronises.
+ */
+bbc_status bbc_graph_work(bbc_graph *g, uint64_t *out, void *cuda_stream);
+
 /* Motif kinds of bbc_count_motif. */
 enum {
     BBC_MOTIF_SIGN_CLASSES = 1, /* the six sign classes of Sec. VII, Table 7 */

@@ -40,7 +40,7 @@ EXPORTS = (
     "bbc_count_noalloc", "bbc_count_motif", "bbc_cost_model_create", "bbc_cost_model_free",
     "bbc_cost_model_num_params", "bbc_cost_model_get_params", "bbc_cost_model_set_params",
     "bbc_cost_model_loss_grad", "bbc_cost_model_fit", "bbc_cost_model_predict", "bbc_item_features",
-    "bbc_item_cycles", "bbc_cost_model_order", "bbc_count_delta",
+    "bbc_item_cycles", "bbc_cost_model_order", "bbc_count_delta", "bbc_graph_work",
 )
 
 MOTIF_SIGN_CLASSES = 1
@@ -125,6 +125,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "bbc_item_features": ([vp, vp, i32, ctypes.POINTER(i32), vp], ctypes.c_int),
             "bbc_item_cycles": ([vp, vp, i32, ctypes.POINTER(i32), vp], ctypes.c_int),
             "bbc_cost_model_order": ([vp, vp, vp], ctypes.c_int),
+            "bbc_graph_work": ([vp, vp, vp], ctypes.c_int),
             "bbc_count_delta": ([vp, i64, vp, vp, vp, u32, ctypes.POINTER(i64), ctypes.POINTER(i64), vp],
                                 ctypes.c_int),
         }
@@ -292,6 +293,14 @@ class Graph:
         check(lib.bbc_count_motif(self.handle, kind_id, int(k), ctypes.addressof(out),
                                   _stream_ptr(stream)), "bbc_count_motif")
         return tuple(int(x) for x in out[:6 if kind_id == MOTIF_SIGN_CLASSES else 2])
+
+    def work(self, stream=None) -> dict:
+        """{path: (items, wedges, pair-side edges)} of the current work lists."""
+        out = (ctypes.c_uint64 * 12)()
+        check(load().bbc_graph_work(self.handle, ctypes.addressof(out), _stream_ptr(stream)),
+              "bbc_graph_work")
+        names = ("k_tile", "k_group_tile", "k_warp_tile", "k_warp_hash")
+        return {n: (int(out[3 * k]), int(out[3 * k + 1]), int(out[3 * k + 2])) for k, n in enumerate(names)}
 
     def count_delta(self, u, v, new_sign, stream=None) -> tuple:
         """(change in balanced, change in unbalanced butterflies) if edge (u[i], v[i]) took

@@ -58,6 +58,33 @@ __global__ void k_scatter_per_vertex(const unsigned long long *__restrict__ by_r
 }  // namespace
 
 // Fails unless the current device is a usable GB300 (compute capability 10.3).
+// Wedges and pair-side edges of the anchors behind a work list (one entry per anchor:
+// a tile anchor's first item, or its single hash / warp-tile / group-tile item).
+__global__ void k_work_tile(const TileItem *__restrict__ items, int n, const int64_t *__restrict__ rowS_off,
+                            const unsigned long long *__restrict__ wl, unsigned long long *__restrict__ out) {
+    unsigned long long w = 0, e = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const TileItem it = items[i];
+        if (it.tile_begin != 0) continue;
+        w += wl[it.anchor];
+        e += (unsigned long long)(rowS_off[it.anchor + 1] - rowS_off[it.anchor]);
+    }
+    if (w) atomicAdd(out, w);
+    if (e) atomicAdd(out + 1, e);
+}
+
+__global__ void k_work_hash(const HashItem *__restrict__ items, int n, const int64_t *__restrict__ rowS_off,
+                            const unsigned long long *__restrict__ wl, unsigned long long *__restrict__ out) {
+    unsigned long long w = 0, e = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const HashItem it = items[i];
+        w += wl[it.anchor];
+        e += (unsigned long long)(rowS_off[it.anchor + 1] - rowS_off[it.anchor]);
+    }
+    if (w) atomicAdd(out, w);
+    if (e) atomicAdd(out + 1, e);
+}
+
 bbc_status check_device() {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -426,6 +453,55 @@ bbc_status bbc_count_motif(bbc_graph *g, int32_t kind, int32_t k, uint64_t *out,
         return BBC_OK;
     } catch (...) {
         set_error("unexpected exception in bbc_count_motif");
+        return BBC_E_CUDA;
+    }
+}
+
+bbc_status bbc_graph_work(bbc_graph *g, uint64_t *out, void *cuda_stream) {
+    if (!g || !out) {
+        set_error("bbc_graph_work: NULL graph or NULL output");
+        return BBC_E_INVALID_ARG;
+    }
+    try {
+        cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+        if (!g->items_valid) {
+            const int sms = device_sm_count();
+            Tuning T = resolve_tuning(nullptr, sms);
+            T.split_wedges = auto_split(g->wedges, sms, T.blocks_per_sm);
+            BBC_TRY(build_work_lists(g, T, st));
+        }
+        unsigned long long *d = nullptr;
+        BBC_TRY(dev_alloc_n(&d, 8, st));
+        bbc_status rc = BBC_OK;
+        unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        cudaError_t e = cudaMemsetAsync(d, 0, 64, st);
+        const int nl[4] = {g->n_tile, g->n_gt, g->n_wt, g->n_warp};
+        if (e == cudaSuccess && g->n_tile > 0) {
+            note_launch();
+            k_work_tile<<<std::min((g->n_tile + 255) / 256, 1024), 256, 0, st>>>(g->tile_items, g->n_tile,
+                                                                                  g->rowS_off, g->wl, d);
+        }
+        const HashItem *lists[3] = {g->gt_items, g->wt_items, g->warp_items};
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+            if (nl[k + 1] > 0) {
+                note_launch();
+                k_work_hash<<<std::min((nl[k + 1] + 255) / 256, 1024), 256, 0, st>>>(lists[k], nl[k + 1],
+                                                                                    g->rowS_off, g->wl, d + 2 * (k + 1));
+            }
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, 64, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "bbc_graph_work");
+        dev_free(d, st);
+        if (rc != BBC_OK) return rc;
+        for (int k = 0; k < 4; ++k) {
+            out[3 * k] = (uint64_t)nl[k];
+            out[3 * k + 1] = h[2 * k];
+            out[3 * k + 2] = h[2 * k + 1];
+        }
+        return BBC_OK;
+    } catch (...) {
+        set_error("unexpected exception in bbc_graph_work");
         return BBC_E_CUDA;
     }
 }
