@@ -169,22 +169,26 @@ def make_workload():
 
 def oracle_sample(g, target_s: float):
     """Times the oracle on a strided anchor sample sized for about target_s seconds.
+    Every oracle call first builds its adjacency arrays, a fixed cost that one light
+    anchor measures; the stride is then sized on the counting time above that cost.
     Returns (wedges per second, wedges visited, seconds, threads, stride)."""
     import oracle
 
     threads = os.cpu_count() or 1
 
-    def run(stride):
+    def run(stride, offset=0):
         t0 = time.perf_counter()
-        _, w = oracle.count_sample(g, stride=stride, threads=threads, per_vertex=True)
+        _, w = oracle.count_sample(g, stride=stride, offset=offset, threads=threads, per_vertex=True)
         return w, time.perf_counter() - t0
 
+    _, t_fixed = run(g.n_u, offset=g.n_u - 1)
     stride = 8192
     w, dt = run(stride)
-    while dt < 0.5 and stride > 1:
+    while dt - t_fixed < 0.5 and stride > 1:
         stride = max(1, stride // 8)
         w, dt = run(stride)
-    stride = max(1, int(stride * dt / target_s))
+    work_s = max(dt - t_fixed, 1e-3)
+    stride = max(1, int(stride * work_s / max(target_s - t_fixed, 1.0)))
     w, dt = run(stride)
     return w / dt, w, dt, threads, stride
 

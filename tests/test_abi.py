@@ -71,4 +71,13 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
     out = (ctypes.c_uint64 * 6)()
     assert lib.bbc_count_motif(None, 1, 2, ctypes.addressof(out), None) == 1
     assert b"bbc_count_motif" in lib.bbc_last_error()
+    d = ctypes.c_int64()
+    assert lib.bbc_count_delta(None, 0, None, None, None, 0, ctypes.byref(d), None, None) == 1
+    assert lib.bbc_graph_work(None, ctypes.addressof(out), None) == 1
+    assert lib.bbc_cost_model_create(0, None) == 1
+    assert lib.bbc_cost_model_get_params(None, None, 0) == 1
+    assert lib.bbc_cost_model_order(None, None, None) == 1
+    assert lib.bbc_item_features(None, None, 0, None, None) == 1
+    assert lib.bbc_cost_model_num_params() == 1377
+    lib.bbc_cost_model_free(None)
     lib.bbc_graph_free(None)
