@@ -856,6 +856,45 @@ __device__ __forceinline__ void group_sync(int grp) {
 // A group of GW warps with a dense counter table of GW * kWtWords words counts one anchor
 // whose whole endpoint range fits the table (single-tile anchors of small and mid-sized
 // graphs): the group's warps share its centre batches, and no block barrier is involved.
+// Totals of a warp or group tile's endpoints [0, n) without per-vertex updates, 16 bytes
+// per thread at a time, then cleared (the block tile's epilogue arithmetic: three dp4a
+// per word of 8-bit counters). Words past the span stay zero: nothing bumps them.
+template <int CW>
+__device__ __forceinline__ void small_tile_totals(uint32_t *tile, uint32_t n, int t, int nt,
+                                                  unsigned long long &bal, unsigned long long &unb) {
+    const uint32_t words = CW == 0 ? (n + 1) / 2 : (CW == 1 ? n : 2 * n);
+    const uint32_t n4 = (words + 3) / 4;
+    uint4 *t4 = reinterpret_cast<uint4 *>(tile);
+    for (uint32_t i = t; i < n4; i += nt) {
+        const uint4 q = t4[i];
+        if ((q.x | q.y | q.z | q.w) == 0) continue;
+        t4[i] = make_uint4(0u, 0u, 0u, 0u);
+        if (CW == 0) {
+            const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+            uint32_t sq = 0, s1 = 0, pn2 = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                sq = __dp4a(w4[k], w4[k], sq);
+                s1 = __dp4a(w4[k], 0x01010101u, s1);
+                pn2 = __dp4a(w4[k], __byte_perm(w4[k], 0u, 0x2301), pn2);
+            }
+            bal += (sq - s1) >> 1;
+            unb += pn2 >> 1;
+        } else if (CW == 1) {
+            const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t p = w4[k] & 0xffffu, m = w4[k] >> 16;
+                bal += ((p * (p - (p > 0))) >> 1) + ((m * (m - (m > 0))) >> 1);
+                unb += p * m;
+            }
+        } else {
+            bal += choose2(q.x) + choose2(q.y) + choose2(q.z) + choose2(q.w);
+            unb += (unsigned long long)q.x * q.y + (unsigned long long)q.z * q.w;
+        }
+    }
+}
+
 template <int GW, int CW>
 __device__ void group_tile_item(const DevGraph &G, int a, uint32_t *tile, int grp, int *batch_ctr,
                                 uint32_t *sacc, WarpStage &ws) {
@@ -877,7 +916,9 @@ __device__ void group_tile_item(const DevGraph &G, int a, uint32_t *tile, int gr
     }
     const uint32_t n = hi - lo;
     unsigned long long bal = 0, unb = 0;
-    if (CW == 2) {
+    if (!G.bS) {
+        small_tile_totals<CW>(tile, n, gt, GW * 32, bal, unb);
+    } else if (CW == 2) {
         for (uint32_t i = gt; i < n; i += GW * 32) {
             const uint32_t p = tile[2 * i], m = tile[2 * i + 1];
             if ((p | m) == 0) continue;
