@@ -212,6 +212,8 @@ bbc_status build_plan(int32_t n, bbc_graph *const *gs, const Tuning &T, std::uni
     L.queue = P->queue;
     L.tuning = T;
     P->launch = L;
+    BBC_TRY(configure_count_kernels());
+    BBC_TRY(ensure_side_streams());   // no stream or event creation inside the capture
     BBC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     cudaMemsetAsync(P->totals, 0, sizeof(unsigned long long) * 2 * (size_t)n, st);
     cudaMemsetAsync(P->queue, 0, sizeof(QueueState), st);

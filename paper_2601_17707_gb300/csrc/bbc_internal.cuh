@@ -200,6 +200,8 @@ bbc_status concat_items(const std::vector<CopyJob> &jobs, bool tiles, void *dst,
 
 // Queues the counting kernels (block tiles, warp tiles, warp hash) on `st`.
 bbc_status launch_count(const CountLaunch &L, cudaStream_t st);
+// Creates the calling thread's side streams for launch_count ahead of a stream capture.
+bbc_status ensure_side_streams();
 
 // Launches only the tile kernel over `items` with `blocks` persistent blocks; touches no
 // memory but the arguments it is given.

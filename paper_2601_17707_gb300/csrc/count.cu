@@ -1177,6 +1177,40 @@ bbc_status configure_count_kernels() {
     return BBC_OK;
 }
 
+// Side streams of the calling host thread on the current device: the smaller count
+// kernels fork off the caller's stream and join back into it, so each one starts on the
+// SMs that the previous one's draining blocks free (inside stream capture the fork and
+// join become graph edges).
+struct SideStreams {
+    int dev = -1;
+    cudaStream_t s[3] = {};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[3] = {};
+};
+
+bbc_status side_streams(SideStreams *&out) {
+    static thread_local SideStreams ss;
+    int dev = 0;
+    BBC_CUDA_TRY(cudaGetDevice(&dev));
+    if (ss.dev != dev) {
+        SideStreams fresh;
+        for (int i = 0; i < 3; ++i) {
+            BBC_CUDA_TRY(cudaStreamCreateWithFlags(&fresh.s[i], cudaStreamNonBlocking));
+            BBC_CUDA_TRY(cudaEventCreateWithFlags(&fresh.join[i], cudaEventDisableTiming));
+        }
+        BBC_CUDA_TRY(cudaEventCreateWithFlags(&fresh.fork, cudaEventDisableTiming));
+        fresh.dev = dev;
+        ss = fresh;
+    }
+    out = &ss;
+    return BBC_OK;
+}
+
+bbc_status ensure_side_streams() {
+    SideStreams *ss = nullptr;
+    return side_streams(ss);
+}
+
 bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
     BBC_TRY(configure_count_kernels());
     const int sms = device_sm_count();
@@ -1193,7 +1227,31 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
         BBC_CUDA_TRY(cudaGetLastError());
         profile_end(tok, st);
     }
+    // the smaller kernels: each on its own side stream when more than one kernel runs and
+    // no per-kernel profile is being taken (it times kernels one after another)
+    const int n_small = (L.n_gt_items > 0) + (L.n_wt_items > 0) + (L.n_warp_items > 0);
+    const bool fork = n_small > 0 && (L.n_tile_items > 0 || n_small > 1) && !profiling_active();
+    SideStreams *ss = nullptr;
+    if (fork) {
+        BBC_TRY(side_streams(ss));
+        BBC_CUDA_TRY(cudaEventRecord(ss->fork, st));
+    }
+    int side = 0;
+    cudaStream_t main_st = st;
+    auto begin_side = [&]() -> cudaStream_t {
+        if (!fork) return main_st;
+        cudaStreamWaitEvent(ss->s[side], ss->fork, 0);
+        return ss->s[side];
+    };
+    auto end_side = [&](cudaStream_t s2) -> bbc_status {
+        if (!fork) return BBC_OK;
+        BBC_CUDA_TRY(cudaEventRecord(ss->join[side], s2));
+        BBC_CUDA_TRY(cudaStreamWaitEvent(main_st, ss->join[side], 0));
+        ++side;
+        return BBC_OK;
+    };
     if (L.n_gt_items > 0) {
+        cudaStream_t st = begin_side();
         const int tok = profile_begin(kProfGroupTile, st);
         note_launch();
         constexpr int groups = kWtWarps / kGroupWarps;
@@ -1202,8 +1260,10 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
             L.graphs, L.gt_items, L.n_gt_items, &L.queue->gt_head);
         BBC_CUDA_TRY(cudaGetLastError());
         profile_end(tok, st);
+        BBC_TRY(end_side(st));
     }
     if (L.n_wt_items > 0) {
+        cudaStream_t st = begin_side();
         const int tok = profile_begin(kProfWarpTile, st);
         note_launch();
         k_group_tile<1><<<std::min((L.n_wt_items + kWtWarps - 1) / kWtWarps, sms * 2), kWtThreads,
@@ -1211,8 +1271,10 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
             L.graphs, L.wt_items, L.n_wt_items, &L.queue->wt_head);
         BBC_CUDA_TRY(cudaGetLastError());
         profile_end(tok, st);
+        BBC_TRY(end_side(st));
     }
     if (L.n_warp_items > 0) {
+        cudaStream_t st = begin_side();
         const int tok = profile_begin(kProfHash, st);
         note_launch();
         k_warp_hash<<<std::min((L.n_warp_items + kHashWarps - 1) / kHashWarps, sms * 3), kHashThreads,
@@ -1220,6 +1282,7 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
             L.graphs, L.warp_items, L.n_warp_items, L.queue);
         BBC_CUDA_TRY(cudaGetLastError());
         profile_end(tok, st);
+        BBC_TRY(end_side(st));
     }
     return BBC_OK;
 }
