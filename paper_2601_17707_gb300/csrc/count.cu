@@ -670,6 +670,8 @@ __device__ __forceinline__ void tile_epilogue(uint32_t *tile, uint32_t lo, uint3
             if (bS) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
+                    // a word whose four counts are all at most 1 closes no butterfly
+                    if ((w4[k] & 0xfefefefeu) == 0) continue;
                     const uint32_t lo16 = w4[k] & 0xffffu, hi16 = w4[k] >> 16;
                     const uint32_t f0 = (__dp4a(lo16, lo16, 0u) - __dp4a(lo16, 0x0101u, 0u)) >> 1;
                     const uint32_t f1 = (__dp4a(hi16, hi16, 0u) - __dp4a(hi16, 0x0101u, 0u)) >> 1;
