@@ -522,7 +522,6 @@ bbc_status bbc_item_cycles(bbc_graph *g, int64_t *cycles_dev, int32_t capacity, 
             set_error("bbc_item_cycles: capacity below the number of tile items");
             return BBC_E_INVALID_ARG;
         }
-        const int sms = device_sm_count();
         BBC_CUDA_TRY(cudaMemsetAsync(g->totals, 0, 16, st));
         BBC_CUDA_TRY(cudaMemsetAsync(g->queue, 0, sizeof(QueueState), st));
         if (g->n_tile > 0) BBC_CUDA_TRY(cudaMemsetAsync(cycles_dev, 0, (size_t)g->n_tile * 8, st));
@@ -537,7 +536,6 @@ bbc_status bbc_item_cycles(bbc_graph *g, int64_t *cycles_dev, int32_t capacity, 
         if (L.tuning.blocks_per_sm < 1) L.tuning.blocks_per_sm = 2;
         L.tuning.plain = 0;
         L.item_cycles = reinterpret_cast<long long *>(cycles_dev);
-        (void)sms;
         BBC_TRY(launch_count(L, st));
         BBC_CUDA_TRY(cudaStreamSynchronize(st));
         return BBC_OK;

@@ -157,7 +157,7 @@ struct DeltaArgs {
     const uint8_t *kold, *knew;
     int64_t n_upd;
     // updates in a order (centre and codes), with the distinct anchors and their segments
-    const uint32_t *a_sorted, *c_by_a;
+    const uint32_t *c_by_a;
     const uint8_t *old_by_a, *new_by_a;
     const uint32_t *anchors, *seg_begin;
     int32_t n_anchors;
@@ -475,7 +475,7 @@ extern "C" bbc_status bbc_count_delta(const bbc_graph *g, int64_t n_updates, con
         BBC_TRY(B.get(&cnt, (size_t)blocks * 4 * (size_t)std::max<int64_t>(nS, 1)));
         BBC_CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)blocks * 16 * (size_t)std::max<int64_t>(nS, 1), st));
         DeltaArgs A{g->rowS_off, g->rowS, g->rowC_off, g->rowC, nS, key, kold, knew, n,
-                    k1, c_by_a, old_by_a, new_by_a, anchors, seg, (int32_t)n_anchors, in_a,
+                    c_by_a, old_by_a, new_by_a, anchors, seg, (int32_t)n_anchors, in_a,
                     cnt, next, out};
         note_launch();
         k_delta_anchor<<<(unsigned)blocks, kDeltaThreads, 0, st>>>(A);
