@@ -201,3 +201,23 @@ def test_side_choice_follows_wedge_cost(gpu_lib):
     G.free()
     assert info.side == (0 if cost_u <= cost_v else 1)
     assert info.wedges == min(cost_u, cost_v)
+
+
+def test_work_statistics_cover_every_wedge(gpu_lib):
+    """The per-path work behind the bench's per-kernel fractions: over the four paths the
+    anchors' oriented wedges add up to W, and their pair-side edges to at most |E|; the
+    sum does not depend on the tuning that split the paths."""
+    g = synth.powerlaw_1m_200k(seed=9, scale=0.02)
+    G = bbc.Graph.from_synthetic(g)
+    try:
+        W = G.info().wedges
+        work = G.work()
+        assert sum(w for _, w, _ in work.values()) == W
+        assert sum(e for _, _, e in work.values()) <= g.n_edges
+        t = bbc.default_tuning()
+        t.warp_max_wedges = 1
+        t.tile_words = 2048
+        G.count(tuning=t)                                   # rebuilds the lists
+        assert sum(w for _, w, _ in G.work().values()) == W
+    finally:
+        G.free()
