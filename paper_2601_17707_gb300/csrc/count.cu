@@ -36,7 +36,8 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kTileThreads = 512;
 constexpr int kTileWarps = kTileThreads / 32;
 constexpr int kChunk = kTileThreads;      // centres per block-sweep chunk
-constexpr int kLongMin = 64;              // slices this long are cut into pieces
+constexpr int kLongMin = 64;
+              // slices this long are cut into pieces
 constexpr int kPiece = 1024;              // wedges per piece of a long slice
 constexpr int kLongSlice = 64;            // warp sweep: slices this long use the whole warp
 constexpr int kWtThreads = 512;          // warp-tile kernel: 16 warps, one table each
@@ -353,12 +354,30 @@ struct ChunkSmem {
     uint32_t start[kChunk];
     uint32_t len[kChunk];
     uint32_t ent[kChunk];
-    uint32_t pshort[kChunk + 1];
     uint32_t ppiece[kChunk + 1];
+    // the chunk's non-empty short slices, compacted in centre order: concatenated start
+    // (sP[nz] = ns, the chunk's short-wedge total), rowC index minus that start, and the
+    // centre's sign bit | its index in the chunk
+    uint32_t sP[kChunk + 1];
+    uint32_t sbase[kChunk];
+    uint32_t smeta[kChunk];
     unsigned long long acc[kChunk];
     unsigned long long wsum[kTileWarps];
+    uint32_t ns, nz;
     int piece_ctr;
 };
+// index of the last entry <= k in the non-decreasing p[0..n] (p[0] == 0 <= k)
+__device__ __forceinline__ int last_le_n(const uint32_t *p, int n, uint32_t k) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p[mid] <= k)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
 
 __device__ __forceinline__ unsigned long long block_exclusive_scan_u64(unsigned long long x,
                                                                       unsigned long long *total,
@@ -515,67 +534,78 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
                 find_slice(G, ci, ci - sb, X, start, len);
             }
             const bool islong = len >= (uint32_t)kLongMin;
+            const uint32_t slen = islong ? 0u : len;
+            // fields: pieces (bits 32..63), non-empty short slices (16..31), short wedges
+            // (0..15; at most 63 per centre, so the chunk's sum stays below 2^15)
             const unsigned long long mine =
                 ((unsigned long long)(islong ? (len + kPiece - 1) / kPiece : 0u) << 32) |
-                (islong ? 0u : len);
+                ((unsigned long long)(slen != 0u) << 16) | slen;
             __shared__ unsigned long long s_total;
             const unsigned long long ex = block_exclusive_scan_u64(mine, &s_total, cs.wsum);
             cs.start[tid] = start;
             cs.len[tid] = len;
             cs.ent[tid] = ent;
-            cs.pshort[tid] = (uint32_t)ex;
             cs.ppiece[tid] = (uint32_t)(ex >> 32);
+            if (slen) {
+                const uint32_t c = (uint32_t)(ex >> 16) & 0xffffu, off = (uint32_t)ex & 0xffffu;
+                cs.sP[c] = off;
+                cs.sbase[c] = start - off;
+                cs.smeta[c] = (ent & kSignBit) | (uint32_t)tid;
+            }
             if (MODE == 1) cs.acc[tid] = 0;
             if (tid == 0) cs.piece_ctr = 0;
             const unsigned long long total = s_total;
             if (tid == kChunk - 1) {
-                cs.pshort[kChunk] = (uint32_t)total;
+                const uint32_t nz = (uint32_t)(total >> 16) & 0xffffu;
                 cs.ppiece[kChunk] = (uint32_t)(total >> 32);
+                cs.ns = (uint32_t)total & 0xffffu;
+                cs.nz = nz;
+                cs.sP[nz] = (uint32_t)total & 0xffffu;
             }
             __syncthreads();
         }
-        const uint32_t NS = cs.pshort[kChunk], NP = cs.ppiece[kChunk];
-        // short slices: contiguous equal shares, the next entry's load issued before the
-        // current entry's counter update
+        const uint32_t NS = cs.ns, NP = cs.ppiece[kChunk];
+        // short slices: each warp takes an equal contiguous range of the chunk's
+        // concatenated short wedges and walks it 32 at a time, lane L on position r + L,
+        // so a slice's entries are read by consecutive lanes (coalesced). A lane's slice
+        // is its window's first slice plus the number of slice ends at or before its
+        // position, counted from a bit mask of the ends inside the window.
         if (NS) {
-            uint32_t k = (uint32_t)(((unsigned long long)NS * tid) / kChunk);
-            const uint32_t k1 = (uint32_t)(((unsigned long long)NS * (tid + 1)) / kChunk);
-            if (k < k1) {
-                int j = last_le(cs.pshort, k);
-                uint32_t nb = cs.pshort[j + 1];
-                uint32_t base = cs.start[j] - cs.pshort[j];
-                uint32_t sg = cs.ent[j] & kSignBit;
-                Acc<CW> acc = 0;
-                uint32_t x = __ldg(rowC + (uint32_t)(base + k));
-                for (;;) {
-                    const uint32_t k2 = k + 1;
-                    int j2 = j;
-                    uint32_t nb2 = nb, base2 = base, sg2 = sg, x2 = 0;
-                    if (k2 < k1) {
-                        if (k2 >= nb2) {
-                            do {
-                                ++j2;
-                                nb2 = cs.pshort[j2 + 1];
-                            } while (nb2 <= k2);
-                            base2 = cs.start[j2] - cs.pshort[j2];
-                            sg2 = cs.ent[j2] & kSignBit;
+            const int warp = tid >> 5;
+            const uint32_t r0 = (uint32_t)(((unsigned long long)NS * warp) / kTileWarps);
+            const uint32_t r1 = (uint32_t)(((unsigned long long)NS * (warp + 1)) / kTileWarps);
+            if (r0 < r1) {
+                const int nz = (int)cs.nz;
+                int j0 = last_le_n(cs.sP, nz, r0);
+                for (uint32_t r = r0; r < r1; r += 32u) {
+                    // ends of the (up to) 32 slices after j0; each is > r
+                    const int jl = j0 + 1 + lane;
+                    const uint32_t e = jl <= nz ? cs.sP[jl] : 0xffffffffu;
+                    const uint32_t d = e - r;
+                    const uint32_t m = __reduce_or_sync(kFull, d < 32u ? 1u << d : 0u);
+                    const bool at32 = __any_sync(kFull, d == 32u);
+                    const uint32_t k = r + lane;
+                    const int j = k < r1 ? j0 + __popc(m & ((2u << lane) - 1u)) : -1;
+                    uint32_t meta = 0;
+                    Acc<CW> v = 0;
+                    if (j >= 0) {
+                        meta = cs.smeta[j];
+                        wedge<MODE, CW>(ctr, __ldg(rowC + (uint32_t)(cs.sbase[j] + k)), meta & kSignBit, v);
+                    }
+                    j0 += __popc(m) + (at32 ? 1 : 0);
+                    if (MODE == 1) {
+                        // segmented sum over lanes of the same slice (contiguous lanes);
+                        // the last lane of each slice adds it
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const Acc<CW> y = __shfl_up_sync(kFull, v, o);
+                            const int jj = __shfl_up_sync(kFull, j, o);
+                            if (lane >= o && jj == j) v += y;
                         }
-                        x2 = __ldg(rowC + (uint32_t)(base2 + k2));
+                        const int jn = __shfl_down_sync(kFull, j, 1);
+                        if (j >= 0 && (lane == 31 || jn != j) && v) acc_add<CW>(cs, (int)(meta & 0x1ffu), v);
                     }
-                    wedge<MODE, CW>(ctr, x, sg, acc);
-                    if (k2 >= k1) break;
-                    if (MODE == 1 && j2 != j && acc) {
-                        acc_add<CW>(cs, j, acc);
-                        acc = 0;
-                    }
-                    k = k2;
-                    j = j2;
-                    nb = nb2;
-                    base = base2;
-                    sg = sg2;
-                    x = x2;
                 }
-                if (MODE == 1 && acc) acc_add<CW>(cs, j, acc);
             }
         }
         // long slices: pieces pulled by warps
