@@ -53,6 +53,40 @@ struct TileItem {
 
 __host__ __device__ inline int tile_end_of(const TileItem &t) { return (int)(t.tile_end_cw & 0x3fffffffu); }
 __host__ __device__ inline int tile_width_of(const TileItem &t) { return (int)(t.tile_end_cw >> 30); }
+
+// Counter widths of a block tile: 0 two 8-bit, 1 two 16-bit, 2 two 32-bit counters per
+// endpoint. A tile item whose width field is kWidthPerTile chooses the width tile by
+// tile: a pair (a, w) shares at most min(deg a, wedges of a, deg w) centres, and degrees
+// fall with rank, so a tile's first endpoint bounds all its counts.
+constexpr int kWidthPerTile = 3;
+__host__ __device__ inline int width_for_bound(unsigned long long bound) {
+    return bound <= 255 ? 0 : (bound <= 65535 ? 1 : 2);
+}
+__host__ __device__ constexpr uint32_t tile_endpoints(int cw, uint32_t tile_words) {
+    return cw == 0 ? tile_words * 2 : (cw == 1 ? tile_words : tile_words / 2);
+}
+struct VarTile {
+    uint32_t lo, hi;   // endpoint ranks [lo, hi)
+    int cw;
+};
+// The tile that starts at endpoint rank lo (< range_hi) of an anchor whose counts are at
+// most bound_a.
+__device__ __forceinline__ VarTile var_tile_at(const int64_t *__restrict__ rowS_off, unsigned long long bound_a,
+                                               uint32_t lo, uint32_t range_hi, uint32_t tile_words) {
+    const unsigned long long d = (unsigned long long)(rowS_off[lo + 1] - rowS_off[lo]);
+    VarTile t;
+    t.lo = lo;
+    t.cw = width_for_bound(d < bound_a ? d : bound_a);
+    const uint32_t e = tile_endpoints(t.cw, tile_words);
+    t.hi = range_hi - lo > e ? lo + e : range_hi;
+    return t;
+}
+__device__ __forceinline__ int var_tile_count(const int64_t *__restrict__ rowS_off, unsigned long long bound_a,
+                                              uint32_t range_lo, uint32_t range_hi, uint32_t tile_words) {
+    int n = 0;
+    for (uint32_t lo = range_lo; lo < range_hi; ++n) lo = var_tile_at(rowS_off, bound_a, lo, range_hi, tile_words).hi;
+    return n;
+}
 __host__ __device__ inline uint32_t pack_tile_end(int end, int cw) {
     return (uint32_t)end | ((uint32_t)cw << 30);
 }

@@ -755,6 +755,52 @@ __device__ void run_tile_item(const DevGraph &G, const TileItem &item, int tile_
     if (centre_carry) red_add(G.bC + (cs.ent[threadIdx.x] & kIdMask), centre_carry);
 }
 
+// One tile [X.lo, X.hi) of an anchor: the count sweep, the centre sweep (per-vertex
+// counts), the epilogue.
+template <int CW>
+__device__ void tile_pass(const DevGraph &G, int64_t sb, int64_t se, const SweepCtx &X, uint32_t *tile,
+                          ChunkSmem &cs, unsigned long long &centre_carry, unsigned long long &bal,
+                          unsigned long long &unb) {
+    const TileCounter<CW> ctr{tile, X.lo};
+    block_sweep<0, CW>(G, sb, se, X, ctr, cs, centre_carry);
+    if (G.bC) block_sweep<1, CW>(G, sb, se, X, ctr, cs, centre_carry);
+    tile_epilogue<CW>(tile, X.lo, X.hi, G.bS, bal, unb);
+    __syncthreads();
+}
+
+// An item whose tiles choose their counter width one by one (the tile boundaries are the
+// same walk that preparation used for the boundary table).
+__device__ void run_tile_item_var(const DevGraph &G, const TileItem &item, int tile_words, uint32_t *tile,
+                                  ChunkSmem &cs, unsigned long long &bal, unsigned long long &unb) {
+    const int a = item.anchor;
+    const int64_t sb = G.rowS_off[a], se = G.rowS_off[a + 1];
+    const unsigned long long deg = (unsigned long long)(se - sb);
+    const unsigned long long bound = deg < G.wl[a] ? deg : G.wl[a];
+    SweepCtx X;
+    X.range_lo = G.orient_low ? 0u : (uint32_t)a + 1u;
+    X.range_hi = G.orient_low ? (uint32_t)a : (uint32_t)G.nS;
+    const int t0 = item.tile_begin, t1 = tile_end_of(item);
+    X.nt = var_tile_count(G.rowS_off, bound, X.range_lo, X.range_hi, (uint32_t)tile_words);
+    X.single = se - sb <= kChunk;
+    X.deg = se - sb;
+    X.bbase = G.boff ? G.boff[a] : 0;
+    VarTile vt = var_tile_at(G.rowS_off, bound, X.range_lo, X.range_hi, (uint32_t)tile_words);
+    for (int t = 0; t < t0; ++t) vt = var_tile_at(G.rowS_off, bound, vt.hi, X.range_hi, (uint32_t)tile_words);
+    unsigned long long centre_carry = 0;   // single chunk: this thread's centre, all tiles
+    for (int t = t0; t < t1; ++t) {
+        X.t = t;
+        X.lo = vt.lo;
+        X.hi = vt.hi;
+        switch (vt.cw) {
+            case 0: tile_pass<0>(G, sb, se, X, tile, cs, centre_carry, bal, unb); break;
+            case 1: tile_pass<1>(G, sb, se, X, tile, cs, centre_carry, bal, unb); break;
+            default: tile_pass<2>(G, sb, se, X, tile, cs, centre_carry, bal, unb); break;
+        }
+        if (t + 1 < t1) vt = var_tile_at(G.rowS_off, bound, vt.hi, X.range_hi, (uint32_t)tile_words);
+    }
+    if (centre_carry) red_add(G.bC + (cs.ent[threadIdx.x] & kIdMask), centre_carry);
+}
+
 // Persistent blocks pop (anchor, tile range) items, heaviest first.
 __global__ void __launch_bounds__(kTileThreads, 2)
 k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, int n_items,
@@ -786,7 +832,8 @@ k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, 
         switch (tile_width_of(item)) {
             case 0: run_tile_item<0>(G, item, tile_words, tile, cs, bal, unb); break;
             case 1: run_tile_item<1>(G, item, tile_words, tile, cs, bal, unb); break;
-            default: run_tile_item<2>(G, item, tile_words, tile, cs, bal, unb); break;
+            case 2: run_tile_item<2>(G, item, tile_words, tile, cs, bal, unb); break;
+            default: run_tile_item_var(G, item, tile_words, tile, cs, bal, unb); break;
         }
         bal = warp_sum(bal);
         unb = warp_sum(unb);

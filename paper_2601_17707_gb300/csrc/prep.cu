@@ -237,6 +237,7 @@ struct ClassifyParams {
     int warp_max;
     long long split;
     int warp_tiles;            // single-tile anchors that fit a warp's table go to k_warp_tile
+    int var_width;             // block tiles choose their counter width tile by tile
 };
 
 // Work of one anchor: kind 0 none, 1 warp-hash item, 2 tile items, 3 warp-tile item (its
@@ -244,9 +245,9 @@ struct ClassifyParams {
 // of warps' pooled table); for tiles, the
 // counter width code (largest reachable count min(degree, wedges) <= 255 / 65535 / more),
 // the number of tiles over its endpoint range and how many items they are split into.
-__device__ __forceinline__ void classify_one(const ClassifyParams &P, unsigned long long wl,
-                                             int64_t deg, int a, int *kind, int *cw, int *ntiles,
-                                             int *groups) {
+__device__ __forceinline__ void classify_one(const ClassifyParams &P, const int64_t *__restrict__ rowS_off,
+                                             unsigned long long wl, int64_t deg, int a, int *kind, int *cw,
+                                             int *ntiles, int *groups, bool count_tiles = true) {
     *kind = 0;
     *cw = 0;
     *ntiles = 0;
@@ -257,26 +258,41 @@ __device__ __forceinline__ void classify_one(const ClassifyParams &P, unsigned l
         return;
     }
     const long long maxcount = deg < (long long)wl ? deg : (long long)wl;
-    const int w = maxcount <= 255 ? 0 : (maxcount <= 65535 ? 1 : 2);
-    const long long ept = w == 0 ? 2ll * P.tile_words : (w == 1 ? P.tile_words : P.tile_words / 2);
+    const int w = width_for_bound((unsigned long long)maxcount);
     const long long span = P.orient_low ? a : (long long)P.nS - 1 - a;
-    const int nt = (int)((span + ept - 1) / ept);
+    if (P.warp_tiles && span <= (long long)group_tile_endpoints(1, w)) {
+        *kind = 3;
+        *cw = w;
+        *ntiles = 1;
+        *groups = 1;
+        return;
+    }
+    if (P.warp_tiles && span <= (long long)group_tile_endpoints(kGroupWarps, w)) {
+        *kind = 4;
+        *cw = w;
+        *ntiles = 1;
+        *groups = 1;
+        return;
+    }
+    int nt;
+    if (P.var_width) {
+        const uint32_t range_lo = P.orient_low ? 0u : (uint32_t)a + 1u;
+        const uint32_t range_hi = P.orient_low ? (uint32_t)a : (uint32_t)P.nS;
+        nt = count_tiles ? var_tile_count(rowS_off, (unsigned long long)maxcount, range_lo, range_hi,
+                                          (uint32_t)P.tile_words)
+                         : 1;
+        *cw = kWidthPerTile;
+    } else {
+        const long long ept = tile_endpoints(w, (uint32_t)P.tile_words);
+        nt = (int)((span + ept - 1) / ept);
+        *cw = w;
+    }
     long long g = 1;
     if ((long long)wl > P.split) g = ((long long)wl + P.split - 1) / P.split;
     if (g > nt) g = nt;
     *kind = 2;
-    *cw = w;
     *ntiles = nt;
     *groups = (int)g;
-    if (P.warp_tiles && span <= (long long)group_tile_endpoints(1, w)) {
-        *kind = 3;
-        *ntiles = 1;
-        *groups = 1;
-    } else if (P.warp_tiles && span <= (long long)group_tile_endpoints(kGroupWarps, w)) {
-        *kind = 4;
-        *ntiles = 1;
-        *groups = 1;
-    }
 }
 
 __global__ void k_classify(ClassifyParams P, const unsigned long long *__restrict__ wl,
@@ -287,7 +303,7 @@ __global__ void k_classify(ClassifyParams P, const unsigned long long *__restric
          a += (int64_t)gridDim.x * blockDim.x) {
         int kind, cw, nt, g;
         const int64_t deg = rowS_off[a + 1] - rowS_off[a];
-        classify_one(P, wl[a], deg, (int)a, &kind, &cw, &nt, &g);
+        classify_one(P, rowS_off, wl[a], deg, (int)a, &kind, &cw, &nt, &g);
         n_tile[a] = kind == 2 ? g : 0;
         n_warp[a] = kind == 1 ? 1 : 0;
         n_wt[a] = kind == 3 ? 1 : 0;
@@ -310,16 +326,24 @@ __global__ void k_tile_bounds(ClassifyParams P, const unsigned long long *__rest
         const uint32_t a = anchor_of[e];
         const int64_t sb = rowS_off[a], deg = rowS_off[a + 1] - sb;
         int kind, cw, nt, g;
-        classify_one(P, wl[a], deg, (int)a, &kind, &cw, &nt, &g);
-        if (kind != 2 || nt <= 1) continue;
-        const uint32_t ept = cw == 0 ? 2u * (uint32_t)P.tile_words
-                                     : (cw == 1 ? (uint32_t)P.tile_words : (uint32_t)P.tile_words / 2u);
+        classify_one(P, rowS_off, wl[a], deg, (int)a, &kind, &cw, &nt, &g, false);
+        if (kind != 2) continue;
         const uint32_t range_lo = P.orient_low ? 0u : a + 1u;
+        const uint32_t range_hi = P.orient_low ? a : (uint32_t)P.nS;
+        const unsigned long long bound = deg < (long long)wl[a] ? (unsigned long long)deg : wl[a];
+        const uint32_t ept = tile_endpoints(cw == kWidthPerTile ? 0 : cw, (uint32_t)P.tile_words);
+        if (cw != kWidthPerTile) nt = (int)((range_hi - range_lo + ept - 1) / ept);
+        uint32_t next = cw == kWidthPerTile
+                            ? var_tile_at(rowS_off, bound, range_lo, range_hi, (uint32_t)P.tile_words).hi
+                            : range_lo + ept;
+        if (next >= range_hi) continue;   // a single tile: no interior boundary
         const uint2 r = rng[e];
         uint32_t pos = r.x;
         uint32_t *dst = bnd + boff[a] + (e - sb);
-        for (int t = 1; t < nt; ++t) {
-            const uint32_t key = range_lo + (uint32_t)t * ept;
+        for (int t = 1; next < range_hi; ++t) {
+            const uint32_t key = next;
+            next = cw == kWidthPerTile ? var_tile_at(rowS_off, bound, key, range_hi, (uint32_t)P.tile_words).hi
+                                       : key + ept;
             uint32_t lo = pos, step = 1;
             while (lo + step <= r.y && (__ldg(rowC + lo + step - 1) & kIdMask) < key) {
                 lo += step;
@@ -351,7 +375,7 @@ __global__ void k_emit_items(ClassifyParams P, const unsigned long long *__restr
          a += (int64_t)gridDim.x * blockDim.x) {
         int kind, cw, nt, g;
         const unsigned long long w = wl[a];
-        classify_one(P, w, rowS_off[a + 1] - rowS_off[a], (int)a, &kind, &cw, &nt, &g);
+        classify_one(P, rowS_off, w, rowS_off[a + 1] - rowS_off[a], (int)a, &kind, &cw, &nt, &g);
         if (kind == 1) {
             warp[pos_warp[a]] = HashItem{0, (int32_t)a, (int32_t)w, 0};
         } else if (kind == 3 || kind == 4) {
@@ -506,7 +530,7 @@ bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
     BBC_TRY(sc.get(&nb, (size_t)nS));
     BBC_TRY(dev_alloc_n(&g->boff, (size_t)nS + 1, st));
     ClassifyParams P{g->nS, g->orient_low, t.tile_words, t.warp_max_wedges, t.split_wedges,
-                     (t.plain || t.tiles_only) ? 0 : 1};
+                     (t.plain || t.tiles_only) ? 0 : 1, t.tiles_only ? 0 : 1};
     note_launch();
     k_classify<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, nt, nh, nb, nw, ng);
     BBC_LAUNCH_CHECK("k_classify");
