@@ -10,15 +10,19 @@
 //
 //   * k_tile: persistent blocks pop (anchor, tile range) items from an atomic queue
 //     (the dynamic scheduling of G-BBC++, Algorithm 4). A tile is a dense shared-memory
-//     counter array over a window of endpoint ranks (Fig. 4's tiles). Because each C -> S
-//     row is sorted by rank, the wedges of centre c that land in the window are one
-//     contiguous slice, found by binary search; a warp sweeps long slices with coalesced
-//     loads and shares short ones across its lanes. Counters are packed: one 32-bit word
-//     per endpoint holding p in the low and n in the high 16 bits (valid while the
-//     anchor's counts stay below 65,536), or a 32-bit pair per endpoint otherwise.
+//     counter array over a window of endpoint ranks (Fig. 4's tiles), with two 8-, 16-
+//     or 32-bit counters per endpoint. The width is chosen tile by tile, since a tile's
+//     first endpoint bounds its counts. Each C -> S row is sorted by rank, so the wedges
+//     of centre c in the window are one contiguous slice. Per chunk of 512 centres, the
+//     short slices are swept by warps with lanes on consecutive positions, and the long
+//     ones in 1,024-wedge pieces with 16-byte loads.
+//   * k_group_tile<4> / k_group_tile<1>: anchors whose whole endpoint range fits a
+//     4-warp group's or one warp's table.
 //   * k_warp_hash: light anchors (few wedges) get one warp each and a small open-
 //     addressing hash table in shared memory, so their cost follows their wedge count
 //     and not the width of their endpoint range.
+//   * k_tile_motif: the same sweep with the counters and epilogue of the sign classes
+//     (Sec. VII) or of balanced (2,k)-bicliques (Def. 5).
 //
 // Per-vertex counts (an extension: the paper defines none) follow from the same
 // counters: the pair {a, w} adds f = C(p,2) + C(n,2) to both b(a) and b(w); and a wedge
