@@ -242,9 +242,10 @@ struct ClassifyParams {
 
 // Work of one anchor: kind 0 none, 1 warp-hash item, 2 tile items, 3 warp-tile item (its
 // whole endpoint range fits one warp's counter table), 4 group-tile item (it fits a group
-// of warps' pooled table); for tiles, the
-// counter width code (largest reachable count min(degree, wedges) <= 255 / 65535 / more),
-// the number of tiles over its endpoint range and how many items they are split into.
+// of warps' pooled table). For tiles: the counter width code (largest reachable count
+// min(degree, wedges) <= 255 / 65535 / more, or kWidthPerTile when the widths are chosen
+// tile by tile), the number of tiles over its endpoint range (not counted, and left at 1,
+// when count_tiles is false) and how many items they are split into.
 __device__ __forceinline__ void classify_one(const ClassifyParams &P, const int64_t *__restrict__ rowS_off,
                                              unsigned long long wl, int64_t deg, int a, int *kind, int *cw,
                                              int *ntiles, int *groups, bool count_tiles = true) {
@@ -313,7 +314,8 @@ __global__ void k_classify(ClassifyParams P, const unsigned long long *__restric
 }
 
 // Interior tile boundaries: for every S -> C entry (a, c) of a tile anchor, the index in
-// row c of the first endpoint of each of a's tiles 1 .. tiles-1, found by galloping from
+// row c of the first endpoint of each of a's tiles 1 .. tiles-1 (the same tile walk as the
+// tile kernel's, with per-tile widths when the item says so), found by galloping from
 // the previous boundary. One thread per entry; the layout (boundary-major per anchor)
 // lets the tile kernel read them coalesced.
 __global__ void k_tile_bounds(ClassifyParams P, const unsigned long long *__restrict__ wl,
