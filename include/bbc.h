@@ -126,7 +126,9 @@ bbc_status bbc_count(bbc_graph *g, uint64_t *balanced, uint64_t *unbalanced, uin
 /*
  * bbc_count_async -- as bbc_count, but writes {balanced, unbalanced} into the device
  * buffer totals_dev (2 x uint64, overwritten) and returns without synchronising.
- * Every launch is queued on `cuda_stream`.
+ * Every launch is queued on `cuda_stream`. The kernels' internal-consistency flag (set
+ * if a light anchor's hash table ran out of slots, which its sizing rules out) is read
+ * back only by the synchronising calls (bbc_count, bbc_count_batch, the server).
  */
 bbc_status bbc_count_async(bbc_graph *g, uint64_t *totals_dev, uint64_t *per_u,
                            uint64_t *per_v, const bbc_tuning *tuning, void *cuda_stream);

@@ -57,7 +57,6 @@ __global__ void k_scatter_per_vertex(const unsigned long long *__restrict__ by_r
 
 }  // namespace
 
-// Fails unless the current device is a usable GB300 (compute capability 10.3).
 // Wedges and pair-side edges of the anchors behind a work list (one entry per anchor:
 // a tile anchor's first item, or its single hash / warp-tile / group-tile item).
 __global__ void k_work_tile(const TileItem *__restrict__ items, int n, const int64_t *__restrict__ rowS_off,
@@ -85,6 +84,7 @@ __global__ void k_work_hash(const HashItem *__restrict__ items, int n, const int
     if (e) atomicAdd(out + 1, e);
 }
 
+// Fails unless the current device is a usable GB300 (compute capability 10.3).
 bbc_status check_device() {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -104,10 +104,6 @@ bbc_status check_device() {
     }
     return BBC_OK;
 }
-
-namespace {
-
-}  // namespace
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
@@ -177,7 +173,12 @@ void dev_free(void *p, cudaStream_t st) {
 
 int device_sm_count() {
     PoolEntry *e = device_entry();
-    return e && e->sms > 0 ? e->sms : 148;
+    if (e && e->sms > 0) return e->sms;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+        return sms;
+    return 152;  // GB300
 }
 
 Tuning resolve_tuning(const bbc_tuning *t, int sm_count) {
@@ -566,10 +567,11 @@ void bbc_graph_free(bbc_graph *g) {
     if (!g) return;
     int prev = 0;
     cudaGetDevice(&prev);
-    if (prev != g->device) cudaSetDevice(g->device);
+    const int dev = g->device;  // release_graph deletes g
+    if (prev != dev) cudaSetDevice(dev);
     release_graph(g, nullptr);
     cudaStreamSynchronize(nullptr);
-    if (prev != g->device) cudaSetDevice(prev);
+    if (prev != dev) cudaSetDevice(prev);
 }
 
 }  // extern "C"

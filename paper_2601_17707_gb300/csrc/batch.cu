@@ -41,7 +41,7 @@ struct Plan {
     int32_t n = 0;
     DevGraph *dgraphs = nullptr;
     unsigned long long *totals = nullptr;     // 2 per graph
-    unsigned long long *host_totals = nullptr;  // pinned
+    unsigned long long *host_totals = nullptr;  // pinned: 2 per graph, then the error word
     QueueState *queue = nullptr;
     TileItem *tiles = nullptr;
     HashItem *warp = nullptr;
@@ -65,6 +65,9 @@ struct Plan {
         if (stream) cudaStreamDestroy(stream);
     }
 };
+
+// The queue's error word, copied back after the totals of each replay.
+unsigned *host_error_word(Plan *p) { return reinterpret_cast<unsigned *>(p->host_totals + 2 * (size_t)p->n); }
 
 std::mutex g_plan_mu;
 std::vector<std::unique_ptr<Plan>> g_plans;  // most recent last; a handful kept
@@ -161,7 +164,8 @@ bbc_status build_plan(int32_t n, bbc_graph *const *gs, const Tuning &T, std::uni
     BBC_TRY(dev_alloc_n(&P->warp, (size_t)nh, st));
     BBC_TRY(dev_alloc_n(&P->wt, (size_t)nw, st));
     BBC_TRY(dev_alloc_n(&P->gt, (size_t)ngr, st));
-    BBC_CUDA_TRY(cudaMallocHost(&P->host_totals, sizeof(unsigned long long) * 2 * (size_t)std::max(n, 1)));
+    BBC_CUDA_TRY(cudaMallocHost(&P->host_totals, sizeof(unsigned long long) * (2 * (size_t)n + 1)));
+    memset(P->host_totals, 0, sizeof(unsigned long long) * (2 * (size_t)n + 1));
     BBC_CUDA_TRY(cudaMemcpyAsync(P->dgraphs, hd.data(), sizeof(DevGraph) * (size_t)n,
                                  cudaMemcpyHostToDevice, st));
     // concatenate, tagging each item with its graph index
@@ -220,6 +224,7 @@ bbc_status build_plan(int32_t n, bbc_graph *const *gs, const Tuning &T, std::uni
     bbc_status ls = launch_count(L, st);
     cudaMemcpyAsync(P->host_totals, P->totals, sizeof(unsigned long long) * 2 * (size_t)n,
                     cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(host_error_word(P.get()), &P->queue->error, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(st, &graph);
     BBC_TRY(ls);
@@ -262,7 +267,14 @@ Plan *find_or_build(int32_t n, bbc_graph *const *gs, const Tuning &T, bbc_status
 bbc_status run_plan(Plan *p, uint64_t *balanced, cudaStream_t st, float *ms) {
     BBC_CUDA_TRY(cudaEventRecord(p->ev_in, st));
     BBC_CUDA_TRY(cudaStreamWaitEvent(p->stream, p->ev_in, 0));
-    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    struct Events {
+        cudaEvent_t t0 = nullptr, t1 = nullptr;
+        ~Events() {
+            if (t0) cudaEventDestroy(t0);
+            if (t1) cudaEventDestroy(t1);
+        }
+    } ev;
+    cudaEvent_t &t0 = ev.t0, &t1 = ev.t1;
     if (ms) {
         BBC_CUDA_TRY(cudaEventCreate(&t0));
         BBC_CUDA_TRY(cudaEventCreate(&t1));
@@ -277,6 +289,8 @@ bbc_status run_plan(Plan *p, uint64_t *balanced, cudaStream_t st, float *ms) {
         BBC_CUDA_TRY(cudaMemcpyAsync(p->host_totals, p->totals,
                                      sizeof(unsigned long long) * 2 * (size_t)p->n,
                                      cudaMemcpyDeviceToHost, p->stream));
+        BBC_CUDA_TRY(cudaMemcpyAsync(host_error_word(p), &p->queue->error, sizeof(unsigned),
+                                     cudaMemcpyDeviceToHost, p->stream));
     } else {
         BBC_CUDA_TRY(cudaGraphLaunch(p->exec, p->stream));
     }
@@ -284,11 +298,11 @@ bbc_status run_plan(Plan *p, uint64_t *balanced, cudaStream_t st, float *ms) {
     BBC_CUDA_TRY(cudaEventRecord(p->ev_out, p->stream));
     BBC_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_out, 0));
     BBC_CUDA_TRY(cudaStreamSynchronize(p->stream));
-    if (ms) {
-        cudaEventElapsedTime(ms, t0, t1);
-        cudaEventDestroy(t0);
-        cudaEventDestroy(t1);
+    if (*host_error_word(p)) {
+        set_error("counting kernel reported an internal inconsistency");
+        return BBC_E_CUDA;
     }
+    if (ms) BBC_CUDA_TRY(cudaEventElapsedTime(ms, t0, t1));
     if (balanced)
         for (int i = 0; i < p->n; ++i) balanced[i] = p->host_totals[2 * i];
     return BBC_OK;

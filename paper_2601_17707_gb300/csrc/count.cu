@@ -43,7 +43,6 @@ constexpr int kChunk = kTileThreads;      // centres per block-sweep chunk
 constexpr int kLongMin = 64;              // slices this long are cut into pieces
 // the chunk scan packs a chunk's short-slice wedges into 16 bits
 static_assert((kLongMin - 1) * kChunk < (1 << 16), "short-slice wedges of a chunk exceed the scan field");
-              // slices this long are cut into pieces
 constexpr int kPiece = 1024;              // wedges per piece of a long slice
 constexpr int kLongSlice = 64;            // warp sweep: slices this long use the whole warp
 constexpr int kWtThreads = 512;          // warp-tile kernel: 16 warps, one table each

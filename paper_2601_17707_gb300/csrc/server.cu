@@ -445,14 +445,14 @@ void bbc_server_destroy(bbc_server *S) {
     if (S->worker.joinable()) S->worker.join();
     for (std::thread &t : S->preppers)
         if (t.joinable()) t.join();
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(S->device);
     for (Request *r : S->ready) {
         if (r->g) release_graph(r->g, S->stream);
         r->g = nullptr;
         finish_locked(S, r, BBC_E_CANCELLED, 0);
     }
-    int prev = 0;
-    cudaGetDevice(&prev);
-    cudaSetDevice(S->device);
     for (Request *r : S->active) {
         if (r->g) release_graph(r->g, S->stream);
         r->g = nullptr;
