@@ -28,6 +28,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -87,11 +88,25 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+_CODE_TOKENS = re.compile(r'"(?:\\.|[^"\\\n])*"|\'(?:\\.|[^\'\\\n])*\'|//[^\n]*|/\*.*?\*/|\s+', re.S)
+
+
+def code_only(text: str) -> str:
+    """The source with comments removed and whitespace runs collapsed, so that the digest
+    below changes with the code and not with its comments (string literals are kept)."""
+    def keep(m):
+        t = m.group(0)
+        if t.startswith("//") or t.startswith("/*"):
+            return " "
+        return " " if t.isspace() else t
+    return " ".join(_CODE_TOKENS.sub(keep, text).split())
+
+
 def kernel_source_digest() -> str:
     h = hashlib.sha256()
     for name in ("count.cu", "bbc_internal.cuh", "graph.cuh"):
-        with open(os.path.join(ROOT, "paper_2601_17707_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2601_17707_gb300", "csrc", name), encoding="utf-8") as f:
+            h.update(code_only(f.read()).encode())
     return h.hexdigest()
 
 
