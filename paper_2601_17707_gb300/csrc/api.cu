@@ -62,7 +62,7 @@ __global__ void k_scatter_per_vertex(const unsigned long long *__restrict__ by_r
 __global__ void k_work_tile(const TileItem *__restrict__ items, int n, const int64_t *__restrict__ rowS_off,
                             const unsigned long long *__restrict__ wl, unsigned long long *__restrict__ out) {
     unsigned long long w = 0, e = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const TileItem it = items[i];
         if (it.tile_begin != 0) continue;
         w += wl[it.anchor];
@@ -75,7 +75,7 @@ __global__ void k_work_tile(const TileItem *__restrict__ items, int n, const int
 __global__ void k_work_hash(const HashItem *__restrict__ items, int n, const int64_t *__restrict__ rowS_off,
                             const unsigned long long *__restrict__ wl, unsigned long long *__restrict__ out) {
     unsigned long long w = 0, e = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const HashItem it = items[i];
         w += wl[it.anchor];
         e += (unsigned long long)(rowS_off[it.anchor + 1] - rowS_off[it.anchor]);

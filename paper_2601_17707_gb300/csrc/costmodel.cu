@@ -64,7 +64,7 @@ inline unsigned grid_blocks(int64_t n_warps_wanted) {
 //   6 log1p(|S|) / 16                7 log1p(wedges * item tiles / anchor tiles) / 16
 __global__ void k_item_features(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items,
                                 int n, int tile_words, float *__restrict__ X) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const TileItem it = items[i];
         const DevGraph &G = graphs[it.graph];
         const int a = it.anchor;
@@ -196,7 +196,7 @@ k_mlp_grad(const float *__restrict__ P, const float *__restrict__ X, const float
 __global__ void k_adam(float *__restrict__ P, const float *__restrict__ G, float *__restrict__ M,
                        float *__restrict__ V, int n, float lr, float beta1, float beta2, float eps,
                        float c1, float c2) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float g = G[i];
         const float m = beta1 * M[i] + (1.f - beta1) * g;
         const float v = beta2 * V[i] + (1.f - beta2) * g * g;
@@ -209,7 +209,7 @@ __global__ void k_adam(float *__restrict__ P, const float *__restrict__ G, float
 // sums[0] += log(c), sums[1] += log(c)^2 over positive cycles
 __global__ void k_label_moments(const long long *__restrict__ cyc, int n, double *__restrict__ sums) {
     double s = 0, q = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double l = log((double)(cyc[i] > 0 ? cyc[i] : 1));
         s += l;
         q += l * l;
@@ -226,14 +226,14 @@ __global__ void k_label_moments(const long long *__restrict__ cyc, int n, double
 }
 
 __global__ void k_labels(const long long *__restrict__ cyc, int n, float mu, float sd, float *__restrict__ t) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         t[i] = (float)((log((double)(cyc[i] > 0 ? cyc[i] : 1)) - mu) / sd);
 }
 
 // Descending order of predictions as ascending 32-bit keys.
 __global__ void k_order_keys(const float *__restrict__ y, int n, uint32_t *__restrict__ keys,
                              uint32_t *__restrict__ idx) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t b = __float_as_uint(y[i]);
         const uint32_t asc = (b & 0x80000000u) ? ~b : (b | 0x80000000u);   // monotone in y
         keys[i] = ~asc;
@@ -243,7 +243,7 @@ __global__ void k_order_keys(const float *__restrict__ y, int n, uint32_t *__res
 
 __global__ void k_gather_tile_items(const TileItem *__restrict__ in, const uint32_t *__restrict__ order,
                                     int n, TileItem *__restrict__ out) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = in[order[i]];
 }
 

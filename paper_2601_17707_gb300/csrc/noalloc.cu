@@ -51,7 +51,7 @@ __global__ void k_noalloc_setup(DevGraph d, NoallocHeader *h, unsigned long long
 __global__ void k_noalloc_items(const unsigned long long *__restrict__ wl,
                                 const int64_t *__restrict__ rowS_off, int nS, int orient_low,
                                 int tile_words, TileItem *__restrict__ items) {
-    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nS; a += gridDim.x * blockDim.x) {
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < nS; a += (int64_t)gridDim.x * blockDim.x) {
         const long long w = (long long)wl[a];
         const long long deg = rowS_off[a + 1] - rowS_off[a];
         int nt = 0, cw = 0;
@@ -62,7 +62,7 @@ __global__ void k_noalloc_items(const unsigned long long *__restrict__ wl,
             const long long span = orient_low ? a : (long long)nS - 1 - a;
             nt = (int)((span + ept - 1) / ept);
         }
-        items[a] = TileItem{0, a, 0, pack_tile_end(nt, cw)};
+        items[a] = TileItem{0, (int32_t)a, 0, pack_tile_end(nt, cw)};
     }
 }
 
