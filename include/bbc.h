@@ -330,6 +330,11 @@ bbc_status bbc_cost_model_predict(const bbc_cost_model *m, const float *X_dev, i
 /* Feature rows of g's tile items (device float[capacity][8]); *n_items = their number.
    X_dev = NULL with capacity 0 only reports the number. */
 bbc_status bbc_item_features(bbc_graph *g, float *X_dev, int32_t capacity, int32_t *n_items, void *cuda_stream);
+/* The original id (on the pair side S, see bbc_graph_info) of each tile item's anchor, in
+   the same queue order (device int32[capacity]); *n_items = their number. Queued, no
+   synchronisation; BBC_E_INVALID_ARG when capacity is below the number of items. */
+bbc_status bbc_item_anchors(bbc_graph *g, int32_t *anchors_dev, int32_t capacity, int32_t *n_items,
+                            void *cuda_stream);
 /*
  * Runs the tile kernel once over g's tile items (global totals only, the other kernels
  * are not run) and writes each item's duration in SM cycles (device int64[capacity]),

@@ -41,6 +41,7 @@ EXPORTS = (
     "bbc_cost_model_num_params", "bbc_cost_model_get_params", "bbc_cost_model_set_params",
     "bbc_cost_model_loss_grad", "bbc_cost_model_fit", "bbc_cost_model_predict", "bbc_item_features",
     "bbc_item_cycles", "bbc_cost_model_order", "bbc_count_delta", "bbc_graph_work",
+    "bbc_item_anchors",
 )
 
 MOTIF_SIGN_CLASSES = 1
@@ -124,6 +125,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "bbc_cost_model_predict": ([vp, vp, i32, vp, vp], ctypes.c_int),
             "bbc_item_features": ([vp, vp, i32, ctypes.POINTER(i32), vp], ctypes.c_int),
             "bbc_item_cycles": ([vp, vp, i32, ctypes.POINTER(i32), vp], ctypes.c_int),
+            "bbc_item_anchors": ([vp, vp, i32, ctypes.POINTER(i32), vp], ctypes.c_int),
             "bbc_cost_model_order": ([vp, vp, vp], ctypes.c_int),
             "bbc_graph_work": ([vp, vp, vp], ctypes.c_int),
             "bbc_count_delta": ([vp, i64, vp, vp, vp, u32, ctypes.POINTER(i64), ctypes.POINTER(i64), vp],
@@ -339,6 +341,19 @@ class Graph:
         check(lib.bbc_item_cycles(self.handle, c.data_ptr(), cap, ctypes.byref(n), _stream_ptr(stream)),
               "bbc_item_cycles")
         return c[: n.value]
+
+    def item_anchors(self, stream=None):
+        """Per tile item, the original pair-side id of its anchor (int32 CUDA tensor, queue
+        order)."""
+        import torch
+
+        lib = load()
+        n = ctypes.c_int32()
+        cap = max(1, self._n_tile_items(stream))
+        a = torch.empty(cap, dtype=torch.int32, device="cuda")
+        check(lib.bbc_item_anchors(self.handle, a.data_ptr(), cap, ctypes.byref(n), _stream_ptr(stream)),
+              "bbc_item_anchors")
+        return a[: n.value]
 
     def _n_tile_items(self, stream=None) -> int:
         lib = load()

@@ -16,6 +16,7 @@
 //     updates (k_adam);
 //   * use: items sorted by predicted cost, heaviest first (bbc_cost_model_order).
 // None of this touches the counting arithmetic: any item order gives the same counts.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -296,6 +297,13 @@ bbc_status item_features(bbc_graph *g, float *X, int capacity, int *n_items, cud
     return BBC_OK;
 }
 
+// The original pair-side id of each tile item's anchor (items hold anchor ranks).
+__global__ void k_item_anchors(const TileItem *__restrict__ items, int n, const int32_t *__restrict__ permS,
+                               int32_t *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = permS[items[i].anchor];
+}
+
 bbc_status ensure_lists(bbc_graph *g, cudaStream_t st) {
     if (g->items_valid) return BBC_OK;
     const int sms = device_sm_count();
@@ -504,6 +512,32 @@ bbc_status bbc_item_features(bbc_graph *g, float *X_dev, int32_t capacity, int32
         return BBC_OK;
     } catch (...) {
         set_error("unexpected exception in bbc_item_features");
+        return BBC_E_CUDA;
+    }
+}
+
+bbc_status bbc_item_anchors(bbc_graph *g, int32_t *anchors_dev, int32_t capacity, int32_t *n_items,
+                            void *cuda_stream) {
+    if (!g || !n_items || (capacity > 0 && !anchors_dev)) {
+        set_error("bbc_item_anchors: NULL argument");
+        return BBC_E_INVALID_ARG;
+    }
+    try {
+        cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+        BBC_TRY(ensure_lists(g, st));
+        *n_items = g->n_tile;
+        if (g->n_tile > capacity) {
+            set_error("bbc_item_anchors: capacity below the number of tile items");
+            return BBC_E_INVALID_ARG;
+        }
+        if (g->n_tile == 0) return BBC_OK;
+        note_launch();
+        k_item_anchors<<<std::min((g->n_tile + 255) / 256, 4096), 256, 0, st>>>(g->tile_items, g->n_tile, g->permS,
+                                                                              anchors_dev);
+        BBC_CUDA_TRY(cudaGetLastError());
+        return BBC_OK;
+    } catch (...) {
+        set_error("unexpected exception in bbc_item_anchors");
         return BBC_E_CUDA;
     }
 }

@@ -78,6 +78,9 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
     assert lib.bbc_cost_model_get_params(None, None, 0) == 1
     assert lib.bbc_cost_model_order(None, None, None) == 1
     assert lib.bbc_item_features(None, None, 0, None, None) == 1
+    n_items = ctypes.c_int32()
+    assert lib.bbc_item_anchors(None, None, 0, ctypes.byref(n_items), None) == 1
+    assert b"bbc_item_anchors" in lib.bbc_last_error()
     assert lib.bbc_cost_model_num_params() == 1377
     lib.bbc_cost_model_free(None)
     lib.bbc_graph_free(None)

@@ -1,7 +1,7 @@
 """GPU tests of the learned cost model: the forward pass and the gradient of the library's
 own kernels against the float64 oracle, training on measured item durations, and what the
-trained network gains over the wedge-share order of the work queue on graphs it was not
-trained on.
+trained network gains over the wedge-share order of the work queue, and over Algorithm 4's
+fanout order, on graphs it was not trained on.
 """
 
 from __future__ import annotations
@@ -48,6 +48,16 @@ def test_forward_and_gradient_match_the_oracle(gpu_lib):
     assert np.array_equal(m.get_params(), p)
 
 
+def _fanout(g, side):
+    """Algorithm 4's queue key on pair side S: fanout(u) = sum over v in N(u) of deg(v),
+    plus deg(u)."""
+    s_ids, c_ids = (g.u, g.v) if side == 0 else (g.v, g.u)
+    n_s, n_c = (g.n_u, g.n_v) if side == 0 else (g.n_v, g.n_u)
+    deg_s = np.bincount(s_ids, minlength=n_s).astype(np.int64)
+    deg_c = np.bincount(c_ids, minlength=n_c).astype(np.int64)
+    return np.bincount(s_ids, weights=deg_c[c_ids], minlength=n_s).astype(np.int64) + deg_s
+
+
 def _items(g):
     G = bbc.Graph.from_synthetic(g)
     X = G.item_features()
@@ -64,6 +74,21 @@ def test_training_reduces_the_loss(gpu_lib):
         start = m.fit(X, c, steps=0)
         end = m.fit(X, c, steps=500, lr=3e-3)
         assert end < 0.5 * start and end < 0.5      # standardised labels: variance 1
+    finally:
+        G.free()
+
+
+def test_item_anchors_match_the_degree_feature(gpu_lib):
+    g = synth.powerlaw_1m_200k(seed=12, scale=0.05)
+    G = bbc.Graph.from_synthetic(g)
+    try:
+        X = G.item_features().cpu().numpy().astype(np.float64)
+        a = G.item_anchors().cpu().numpy().astype(np.int64)
+        side = G.info().side
+        s_ids, n_s = (g.u, g.n_u) if side == 0 else (g.v, g.n_v)
+        assert a.shape[0] == X.shape[0] > 0 and a.min() >= 0 and a.max() < n_s
+        deg = np.bincount(s_ids, minlength=n_s).astype(np.float64)
+        assert np.allclose(X[:, 1], np.log1p(deg[a]) / 16.0, rtol=1e-6, atol=1e-6)
     finally:
         G.free()
 
@@ -90,7 +115,8 @@ def test_what_the_learned_model_gains_over_the_wedge_estimate(gpu_lib):
     compared with the best affine map of the wedge share (least squares on the same
     training items). Ordering the queue by either gives the same makespan here (the
     wedge share already ranks items almost perfectly, and even the true costs leave
-    under 1 % to gain), which the test reports and bounds."""
+    under 1 % to gain), which the test reports and bounds. The paper's own order, by
+    each anchor's fanout (Algorithm 4), is simulated beside them."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     Xs, cs = [], []
     for seed, scale in ((21, 0.05), (22, 0.08), (23, 0.12), (24, 0.15)):
@@ -126,13 +152,17 @@ def test_what_the_learned_model_gains_over_the_wedge_estimate(gpu_lib):
         ms_share = _makespan(np.argsort(-share, kind="stable"), cost, workers)
         ms_model = _makespan(np.argsort(-pred, kind="stable"), cost, workers)
         ms_best = _makespan(np.argsort(-cost, kind="stable"), cost, workers)
+        # Algorithm 4: the items of each anchor in decreasing fanout of the anchor
+        fan = _fanout(g, G.info().side)[G.item_anchors().cpu().numpy().astype(np.int64)]
+        ms_fanout = _makespan(np.argsort(-fan, kind="stable"), cost, workers)
         print(f"held-out log-cycle MSE: network {mse_model:.4f}, affine wedge share {mse_share:.4f}; "
               f"rank correlation: network {rho_model:.3f}, wedge share {rho_share:.3f}; "
-              f"simulated makespan (cycles): wedge order {ms_share:.4g}, learned {ms_model:.4g}, "
-              f"true-cost order {ms_best:.4g}")
+              f"simulated makespan (cycles): fanout order {ms_fanout:.4g}, wedge order {ms_share:.4g}, "
+              f"learned {ms_model:.4g}, true-cost order {ms_best:.4g}")
         assert mse_model < mse_share
         assert rho_model > rho_share - 0.02
         assert ms_model <= 1.02 * ms_share
+        assert ms_model <= 1.02 * ms_fanout
         # the real queue with the learned order: same counts
         before = G.count()[:2]
         m.order(G)
