@@ -337,6 +337,7 @@ WORKLOADS = {
     "uniform_2k_3k_20k": uniform_2k_3k,
     "powerlaw_1m_200k_20m": powerlaw_1m_200k,
     "hubs_50k_2m_100m": hubs_50k_2m,
+    "serve_large_200k_100k_5m": large_serving_graph,
 }
 
 

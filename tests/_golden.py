@@ -64,3 +64,32 @@ def load_cases(name):
 
 def graph(n_u, n_v, edges):
     return _graph(n_u, n_v, edges)
+
+
+def load_batch(name="batch_4096_chung_lu.txt"):
+    """The oracle-written totals of the batched workload: (header dict, list of
+    (n_u, n_v, n_edges, balanced, unbalanced) per member in index order)."""
+    head, rows = {}, []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            t = line.split()
+            if not t or t[0].startswith("#"):
+                continue
+            if t[0] == "g":
+                assert int(t[1]) == len(rows)
+                rows.append(tuple(int(x) for x in t[2:7]))
+            else:
+                head[t[0]] = t[1]
+    return head, rows
+
+
+def load_full(name):
+    """The oracle-written facts of a full-size workload (tests/golden/full_<name>.txt)."""
+    out = {}
+    with open(os.path.join(GOLDEN, f"full_{name}.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, v = line.split()
+            out[k] = v
+    return out
