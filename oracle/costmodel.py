@@ -9,6 +9,13 @@ layer), b2[32], w3[32], b3.
 ``grad`` is backpropagation written out with matrix products (the chain rule layer by
 layer); ``numeric_grad`` is central differences of ``loss``, which shares nothing with it
 but the forward pass, and pins it.
+
+Training: ``standardised_labels`` turns item durations (SM cycles) into the regression
+targets, log(cycles) shifted by their mean and divided by their population standard
+deviation; ``adam_step`` is one update of Adam as Kingma and Ba publish it (ICLR 2015,
+Algorithm 1: exponential moving averages of the gradient and of its square, both divided
+by one minus their decay raised to the step number, then a step of lr times their
+quotient); ``fit`` is that many full-batch Adam steps from given parameters.
 """
 
 from __future__ import annotations
@@ -83,3 +90,39 @@ def numeric_grad(p, X, t, eps: float = 1e-6) -> np.ndarray:
         p[i] = old
         out[i] = (lp - lm) / (2 * eps)
     return out
+
+
+def standardised_labels(cycles):
+    """t_i = (log c_i - mean) / sd over the samples, c_i < 1 read as 1, sd the population
+    standard deviation (floored at 1e-6 so that equal durations do not divide by zero).
+    Returns (t, mean, sd)."""
+    c = np.maximum(np.asarray(cycles, dtype=np.float64), 1.0)
+    lg = np.log(c)
+    mu = float(lg.mean())
+    sd = float(np.sqrt(max(float(np.mean((lg - mu) ** 2)), 1e-12)))
+    return (lg - mu) / sd, mu, sd
+
+
+def adam_step(p, g, m, v, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8):
+    """One Adam update at step number ``step`` (1 for the first). Returns new (p, m, v)."""
+    p = np.asarray(p, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** step)
+    v_hat = v / (1.0 - beta2 ** step)
+    return p - lr * m_hat / (np.sqrt(v_hat) + eps), m, v
+
+
+def fit(p0, X, cycles, steps: int, lr: float):
+    """``steps`` full-batch Adam steps on the mean squared error against the standardised
+    log-cycle labels, from parameters p0 and zero moments. Returns (p, final loss, labels)."""
+    t, _, _ = standardised_labels(cycles)
+    p = np.asarray(p0, dtype=np.float64).copy()
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    for k in range(1, steps + 1):
+        _, g = grad(p, X, t)
+        p, m, v = adam_step(p, g, m, v, k, lr)
+    return p, loss(p, X, t), t

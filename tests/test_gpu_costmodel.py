@@ -48,6 +48,38 @@ def test_forward_and_gradient_match_the_oracle(gpu_lib):
     assert np.array_equal(m.get_params(), p)
 
 
+def test_training_steps_match_the_oracle(gpu_lib):
+    """bbc_cost_model_fit against oracle.costmodel.fit: the standardised log-cycle labels
+    (through the loss at the starting parameters) and the parameters after 1 and after
+    10 full-batch Adam steps (Kingma and Ba's update with bias correction), element by
+    element. Tolerance: at lr = 1e-4 a parameter moves at most 1e-3 in 10 steps; float32
+    gradients (relative error ~1e-5) change each normalised step by about that fraction of
+    lr, so 5e-6 absolute leaves a wide margin, while a missing bias correction (a first
+    step 3.16 lr long) or a wrong moment update misses it by two orders of magnitude."""
+    rng = np.random.default_rng(21)
+    n = 4096
+    X = rng.uniform(0, 1.5, (n, cm.KF)).astype(np.float32)
+    cycles = np.exp(6.0 + 1.5 * X[:, 0] - 0.7 * X[:, 2] + 0.3 * X[:, 5] * X[:, 6]
+                    + 0.1 * rng.normal(size=n)).astype(np.int64)
+    p0 = rng.normal(0, 0.3, cm.N_PARAMS).astype(np.float32)
+    Xd = torch.from_numpy(X).cuda()
+    cd = torch.from_numpy(cycles).cuda()
+    X64 = X.astype(np.float64)
+    for steps in (1, 10):
+        m = bbc.CostModel(seed=3)
+        m.set_params(p0)                     # also clears the moments
+        L0 = m.fit(Xd, cd, steps=0, lr=1e-4)
+        t_ref, _, _ = cm.standardised_labels(cycles)
+        assert L0 == pytest.approx(cm.loss(p0.astype(np.float64), X64, t_ref), rel=1e-4)
+        L = m.fit(Xd, cd, steps=steps, lr=1e-4)
+        p_ref, L_ref, _ = cm.fit(p0.astype(np.float64), X64, cycles, steps=steps, lr=1e-4)
+        got = m.get_params().astype(np.float64)
+        err = np.abs(got - p_ref)
+        assert err.max() <= 5e-6, (steps, int(err.argmax()), float(err.max()))
+        assert L == pytest.approx(L_ref, rel=1e-4)
+        m.free()
+
+
 def _fanout(g, side):
     """Algorithm 4's queue key on pair side S: fanout(u) = sum over v in N(u) of deg(v),
     plus deg(u)."""
