@@ -373,7 +373,8 @@ def per_kernel_roofline(work, prof, passes, peak):
 
 def bench_batched(args, dev):
     """The batched workload: 4,096 Chung-Lu graphs counted by one replay of a captured CUDA
-    graph (autotuned) against per-graph launches of the single-graph path."""
+    graph (autotuned) against per-graph launches of the single-graph path. Every member's
+    count is compared with the oracle-written golden."""
     import torch
 
     from paper_2601_17707_gb300 import bbc, synth
@@ -385,8 +386,9 @@ def bench_batched(args, dev):
     G = [bbc.Graph.from_synthetic(g) for g in gs]
     W = sum(h.info().wedges for h in G)
     E = sum(g.n_edges for g in gs)
-    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
     tuned = bbc.autotune_batch(G)
+    tune_s = time.perf_counter() - t0
     ref = bbc.count_batch(G)                 # builds and caches the plan for the tuned choice
     for _ in range(2):
         bbc.count_batch(G)
@@ -396,7 +398,9 @@ def bench_batched(args, dev):
     for _ in range(reps):
         got = bbc.count_batch(G)
     t_batch = (time.perf_counter() - t0) / reps
-    exact = got == ref
+    consistent = got == ref
+    gold = read_batch_golden()
+    exact = (gold == got) if gold is not None else None
     # per-kernel device times of one batch (launched directly while profiling) and the
     # work behind each path, from the tuned lists the plan used
     bbc.profile_start()
@@ -432,7 +436,7 @@ def bench_batched(args, dev):
     plain.plain = 1
     t_per, ok1 = per_graph(plain)
     t_per_q, ok2 = per_graph(None)
-    exact = exact and ok1 and ok2
+    consistent = consistent and ok1 and ok2
     for h in G:
         h.free()
     return {"workload": "batch_4096_chung_lu", "graphs": len(G), "edges": E, "wedges": W,
@@ -442,26 +446,34 @@ def bench_batched(args, dev):
             "speedup_vs_per_graph_plain": t_per / t_batch,
             "per_graph_queue_graphs_per_s": len(G) / t_per_q, "per_graph_queue_ms": 1e3 * t_per_q,
             "speedup_vs_per_graph_queue": t_per_q / t_batch,
-            "counts_identical": bool(exact), "tuning": tuned.as_dict(), "kernels": kernels,
+            "counts_identical": bool(consistent), "exact": exact,
+            "exact_against": "tests/golden/batch_4096_chung_lu.txt (CPU oracle), every member",
+            "tuning": tuned.as_dict(), "autotune_s": tune_s, "kernels": kernels,
             "timing": f"host wall clock around bbc_count_batch (replay + D2H + sync), mean of "
                       f"{reps}; per-graph: bbc_count_async per graph on one stream, one sync "
                       "(plain = static one-block-per-anchor kernel; queue = work-queue kernel)",
-            "generation_s": gen_s}, gs
+            "generation_s": gen_s}, (gs, gold)
 
 
 def bench_serving(args, pool):
     """Poisson arrivals at several offered rates; 99% of requests from the batch pool,
-    1% large (|U| = 200,000, |V| = 100,000, 5M edges); 8 GB device budget."""
+    1% large (|U| = 200,000, |V| = 100,000, 5M edges); 8 GB device budget. Every ticket is
+    compared with the oracle-written golden of its graph; per rate the record also gives
+    the device time of the counting ticks (busy fraction), the preparation time, the large
+    requests' wedges and times, and the latency of the small requests alone."""
     from paper_2601_17707_gb300 import bbc, synth
 
+    gs, gold = pool
     large = synth.large_serving_graph(seed=0)
+    lg = read_golden("serve_large_200k_100k_5m")
+    large_want = int(lg["balanced"]) if lg is not None else None
     rng = np.random.default_rng(0)
     out = []
     for rate in args.serve_rates:
         n = int(min(args.serve_max_requests, max(200, rate * args.serve_seconds)))
         srv = bbc.Server(8 << 30)
         gaps = rng.exponential(1.0 / rate, size=n)
-        picks = rng.integers(0, len(pool), size=n)
+        picks = rng.integers(0, len(gs), size=n)
         is_large = rng.random(n) < 0.01
         tickets = []
         t_start = time.perf_counter()
@@ -470,35 +482,99 @@ def bench_serving(args, pool):
             t_next += gaps[k]
             while time.perf_counter() < t_next:
                 pass
-            g = large if is_large[k] else pool[picks[k]]
+            g = large if is_large[k] else gs[picks[k]]
             tickets.append(srv.submit(g))
-        for t in tickets:
-            srv.wait(t, timeout_s=600.0)
+        got = [srv.wait(t, timeout_s=600.0) for t in tickets]
         wall = time.perf_counter() - t_start
         st = srv.stats()
+        c = srv.counters()
+        infos = [srv.request_info(t) for t in tickets]
         srv.close()
-        out.append({"offered_graphs_per_s": rate, "requests": n, "large": int(is_large.sum()),
-                    "graphs_per_s": n / wall, "p50_ms": st["p50_us"] / 1e3,
-                    "p99_ms": st["p99_us"] / 1e3, "mean_ms": st["mean_us"] / 1e3})
-    return {"budget_gb": 8, "latency": "submit to completion, library clock", "rates": out}
+        want = [large_want if is_large[k] else (gold[picks[k]] if gold is not None else None)
+                for k in range(n)]
+        exact = None if any(w is None for w in want) else got == want
+        small_lat = sorted(q["latency_us"] for q, L in zip(infos, is_large) if not L)
+        big = [q for q, L in zip(infos, is_large) if L]
+
+        def pct(a, q):
+            return a[min(len(a) - 1, int(q * (len(a) - 1) + 0.5))] / 1e3 if a else None
+
+        out.append({
+            "offered_graphs_per_s": rate, "requests": n, "large": int(is_large.sum()),
+            "graphs_per_s": n / wall, "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
+            "mean_ms": st["mean_us"] / 1e3, "exact": exact,
+            "small_p50_ms": pct(small_lat, 0.5), "small_p99_ms": pct(small_lat, 0.99),
+            "ticks": c["ticks"], "tick_gpu_ms": c["tick_gpu_us"] / 1e3,
+            "tick_wall_ms": c["tick_wall_us"] / 1e3, "prep_wall_ms": c["prep_wall_us"] / 1e3,
+            "gpu_busy_frac": c["tick_gpu_us"] / (wall * 1e6),
+            "tick_thread_busy_frac": c["tick_wall_us"] / (wall * 1e6),
+            "mean_tick_ms": c["tick_wall_us"] / 1e3 / max(1, c["ticks"]),
+            "peak_reserved_gb": c["peak_reserved_bytes"] / 1e9, "max_queued": c["max_queued"],
+            "admitted_after_wait": c["admitted_after_wait"],
+            "large_requests": [{"wedges": q["wedges"], "latency_ms": q["latency_us"] / 1e3,
+                                "queued_ms": q["queued_us"] / 1e3, "prepare_ms": q["prepare_us"] / 1e3,
+                                "count_ms": q["count_us"] / 1e3, "ticks": q["ticks"],
+                                "tick_gpu_ms": q["tick_gpu_us"] / 1e3} for q in big[:3]],
+        })
+    return {"budget_gb": 8, "latency": "submit to completion, library clock",
+            "exact_against": "tests/golden (CPU oracle): batch members and the 5M-edge request",
+            "rates": out}
 
 
-def bench_gpu(args):
+GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
+GOLDEN_NAME = {"powerlaw_1m_200k_20m": "powerlaw_1m_200k_20m", "hubs_50k_2m_100m": "hubs_50k_2m_100m",
+               "uniform_2k_3k": "uniform_2k_3k_20k"}
+
+
+def read_golden(workload: str):
+    """The oracle-written totals and per-vertex digests of a workload (tests/golden/), or
+    None when there is no such file."""
+    path = os.path.join(GOLDEN_DIR, f"full_{GOLDEN_NAME.get(workload, workload)}.txt")
+    if not os.path.exists(path):
+        return None
+    out = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, v = line.split()
+            out[k] = v
+    return out
+
+
+def read_batch_golden():
+    """Per member of the 4,096-graph batch, its oracle-written balanced total (or None)."""
+    path = os.path.join(GOLDEN_DIR, "batch_4096_chung_lu.txt")
+    if not os.path.exists(path):
+        return None
+    rows = []
+    with open(path) as f:
+        for line in f:
+            t = line.split()
+            if t and t[0] == "g":
+                rows.append(int(t[5]))
+    return rows
+
+
+def u64_digest(t) -> str:
+    """SHA-256 of a per-vertex result (int64 CUDA tensor holding uint64 values) as
+    little-endian uint64, the layout of the golden digests."""
+    a = t.cpu().numpy().view(np.uint64)
+    return hashlib.sha256(np.ascontiguousarray(a, dtype="<u8").tobytes()).hexdigest()
+
+
+def single_graph(args, workload, steps, warmup, dev, dist, world, with_e2e):
+    """One single-graph configuration: `steps` timed steps of bbc_prepare + bbc_count with
+    per-vertex counts on device-resident input (the production launch path: no per-kernel
+    events, the side streams live), then a separate pass with per-kernel CUDA events for
+    the roofline figures, a count-only pass, and optionally the same step through host
+    buffers. The last timed step's totals and per-vertex digests are compared with the
+    oracle-written golden."""
     import torch
 
-    from paper_2601_17707_gb300 import _build, bbc
+    from paper_2601_17707_gb300 import bbc
 
-    world, rank, local = dist_env()
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    _build.build()
-    bbc.load()
-    g = make_workload(args.workload)
-    dev = torch.device("cuda", local)
+    g = make_workload(workload)
     u_h = torch.from_numpy(g.u).pin_memory()
     v_h = torch.from_numpy(g.v).pin_memory()
     s_h = torch.from_numpy(g.sign).pin_memory()
@@ -514,6 +590,12 @@ def bench_gpu(args):
     G0 = bbc.Graph.prepare(g.n_u, g.n_v, u_d, v_d, s_d)
     info = G0.info()
     work0 = G0.work()
+    # count-only tile kernel: global totals, no per-vertex pass
+    G0.count_async(totals)
+    bbc.profile_start()
+    for _ in range(3):
+        G0.count_async(totals)
+    prof_co = bbc.profile_stop()
     G0.free()
     W = info.wedges
 
@@ -539,21 +621,21 @@ def bench_gpu(args):
     l2_note = (f"inputs larger than L2: {input_bytes / 1e6:.0f} MB edge list and the CSR per step"
                if flush is None else "L2 flushed (256 MB written) before every timed step, outside the events")
 
-    def timed(fn, steps):
+    def timed(fn, k):
         rank_barrier(dist)
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         if flush is None:
             e0.record(stream)
-            for _ in range(steps):
+            for _ in range(k):
                 fn()
             e1.record(stream)
             torch.cuda.synchronize(dev)
             ms = e0.elapsed_time(e1)
         else:
             ms = 0.0
-            for _ in range(steps):
+            for _ in range(k):
                 flush.fill_(1)
                 e0.record(stream)
                 fn()
@@ -563,44 +645,113 @@ def bench_gpu(args):
         rank_barrier(dist)
         return max_over_ranks(ms, dist, dev)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step_device()
     torch.cuda.synchronize(dev)
     launches0 = bbc.launch_count()
-    bbc.profile_start()
-    with ClockSampler(local) as clk:
-        ms = timed(step_device, args.steps)
-    prof = bbc.profile_stop()
+    with ClockSampler(dev.index if dev.index is not None else 0) as clk:
+        ms = timed(step_device, steps)
     launches = bbc.launch_count() - launches0
-    # correctness of what was timed: the last step's totals against a fresh count
-    b_last = int(totals[0].item())
+    # what the timed steps computed, against the oracle-written golden
+    b_last, ub_last = [int(x) for x in totals.cpu().numpy().view(np.uint64)]
+    gold = read_golden(workload)
+    check = {"balanced": b_last, "unbalanced": ub_last}
+    if gold is not None:
+        check["per_u_sha256_equal"] = u64_digest(per_u) == gold["per_u_sha256"]
+        check["per_v_sha256_equal"] = u64_digest(per_v) == gold["per_v_sha256"]
+        check["exact"] = (b_last == int(gold["balanced"]) and ub_last == int(gold["unbalanced"])
+                          and check["per_u_sha256_equal"] and check["per_v_sha256_equal"])
+        check["against"] = f"tests/golden/full_{GOLDEN_NAME.get(workload, workload)}.txt (CPU oracle)"
+    else:
+        check["exact"] = None
+
+    # per-kernel device times: a separate pass with CUDA events around every counting
+    # kernel (profiling serialises the side streams, so it is not the timed pass)
+    prof_steps = max(1, min(steps, 5))
+    bbc.profile_start()
+    for _ in range(prof_steps):
+        step_device()
+    torch.cuda.synchronize(dev)
+    prof = bbc.profile_stop()
 
     e2e = None
-    if not args.no_e2e:
-        for _ in range(max(1, args.warmup // 2)):
+    if with_e2e:
+        for _ in range(max(1, warmup // 2)):
             step_host()
-        ms_e2e = timed(step_host, args.steps)
-        e2e = {"value": whole_job_rate(world, W, args.steps, ms_e2e), "unit": UNIT,
+        ms_e2e = timed(step_host, steps)
+        e2e = {"value": whole_job_rate(world, W, steps, ms_e2e), "unit": UNIT,
                "h2d_bytes_per_step": g.n_edges * (4 + 4 + 1),
-               "d2h_bytes_per_step": (g.n_u + g.n_v) * 8 + 16, "ms_per_step": ms_e2e / args.steps}
+               "d2h_bytes_per_step": (g.n_u + g.n_v) * 8 + 16, "ms_per_step": ms_e2e / steps}
 
-    tile_launches, tile_ms = prof.get("k_tile", (0, 0.0))
     peak, peak_kind = hbm_peak()
     roof = None
+    tile_launches, tile_ms = prof.get("k_tile", (0, 0.0))
     if tile_launches:
         alg_bytes = 4 * 2 * W + 20 * g.n_edges   # per launch (one launch per step)
-        per_launch_s = tile_ms / tile_launches / 1e3
-        achieved = alg_bytes / per_launch_s / 1e9
+        achieved = alg_bytes / (tile_ms / tile_launches / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": recorded_traffic(args.workload),
+                "frac": achieved / peak, "traffic": recorded_traffic(workload),
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s", "kernel": "k_tile",
                 "kernel_ms_per_launch": tile_ms / tile_launches,
                 "algorithmic_bytes_per_launch": alg_bytes}
+    co = None
+    n_co, ms_co = prof_co.get("k_tile", (0, 0.0))
+    if n_co:
+        alg_co = 4 * W + 20 * g.n_edges
+        ach = alg_co / (ms_co / n_co / 1e3) / 1e9
+        co = {"kernel_ms_per_launch": ms_co / n_co, "algorithmic_bytes_per_launch": alg_co,
+              "achieved": ach, "frac": ach / peak}
+    return {
+        "g": g, "u_d": u_d, "v_d": v_d, "s_d": s_d, "W": W, "info": info, "ms": ms,
+        "value": whole_job_rate(world, W, steps, ms), "ms_per_step": ms / steps, "steps": steps,
+        "warmup": warmup, "launches": launches, "clocks": clk.summary(), "check": check,
+        "roofline": roof, "count_only": co, "kernel_profile": prof,
+        "kernels": per_kernel_roofline(work0, prof, 2, peak), "e2e": e2e, "l2": l2_note,
+        "config": {"workload": workload, "n_u": g.n_u, "n_v": g.n_v, "n_edges": g.n_edges,
+                   "wedges": W, "pair_side": "V" if info.side == 1 else "U", "seed": 0,
+                   "per_vertex": True, "step": "bbc_prepare + bbc_count (global + per-vertex)",
+                   "l2": l2_note},
+    }
+
+
+def bench_gpu(args):
+    import torch
+
+    from paper_2601_17707_gb300 import _build, bbc
+
+    world, rank, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    _build.build()
+    bbc.load()
+    dev = torch.device("cuda", local)
+
+    main = single_graph(args, args.workload, args.steps, args.warmup, dev, dist, world,
+                        with_e2e=not args.no_e2e)
+    g, W = main["g"], main["W"]
+
+    # the other single-graph configurations, each with its own roofline and check
+    others = {}
+    if not args.no_other_configs and world == 1:
+        for wl in WORKLOADS:
+            if wl == args.workload:
+                continue
+            r = single_graph(args, wl, 5 if wl == "hubs_50k_2m_100m" else 20, 3, dev, None, 1,
+                             with_e2e=False)
+            others[wl] = {k: r[k] for k in ("value", "ms_per_step", "steps", "warmup", "check",
+                                            "roofline", "count_only", "kernels", "clocks", "config")}
+            others[wl]["unit"] = UNIT
+            del r
 
     motifs = dynamic = None
     if not args.no_motifs:
-        motifs = bench_motifs(g, u_d, v_d, s_d, W, b_last, int(totals[1].item()))
+        motifs = bench_motifs(g, main["u_d"], main["v_d"], main["s_d"], W,
+                              main["check"]["balanced"], main["check"]["unbalanced"])
         dynamic = bench_dynamic(g)
 
     batched = serving = None
@@ -617,20 +768,23 @@ def bench_gpu(args):
                          f"wedges in {dt:.1f} s"}
 
     if rank == 0:
+        config = dict(main["config"])
+        config["parallelism"] = f"replicas x{world}"
+        config["balanced"] = main["check"]["balanced"]
         line = {
-            "metric": METRIC, "value": whole_job_rate(world, W, args.steps, ms), "unit": UNIT,
+            "metric": METRIC, "value": main["value"], "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": args.workload, "n_u": g.n_u, "n_v": g.n_v, "n_edges": g.n_edges,
-                       "wedges": W, "pair_side": "V" if info.side == 1 else "U", "seed": 0,
-                       "per_vertex": True, "step": "bbc_prepare + bbc_count (global + per-vertex)",
-                       "l2": l2_note,
-                       "parallelism": f"replicas x{world}", "balanced": b_last},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-            "gpu_launches": launches, "kernel_profile": prof,
-            "kernels": per_kernel_roofline(work0, prof, 2, hbm_peak()[0]),
-            "motifs": motifs, "dynamic": dynamic, "batched": batched, "serving": serving,
+            "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": config,
+            "exact": main["check"]["exact"], "check": main["check"],
+            "timing": "value: CUDA events around the timed steps on the production launch path "
+                      "(no per-kernel events); roofline: a separate pass with CUDA events around "
+                      "every counting kernel",
+            "roofline": main["roofline"], "count_only": main["count_only"], "cpu_baseline": cpu,
+            "e2e": main["e2e"], "clocks": main["clocks"], "gpu_launches": main["launches"],
+            "kernel_profile": main["kernel_profile"], "kernels": main["kernels"],
+            "configs": others, "motifs": motifs, "dynamic": dynamic, "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -652,6 +806,8 @@ def main():
     ap.add_argument("--no-motifs", action="store_true",
                     help="skip the sign-class / (2,3) counts and the update-batch delta")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving sweep")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="skip the other two single-graph configurations")
     ap.add_argument("--serve-rates", type=float, nargs="+",
                     default=[100, 300, 1000, 3000, 10000, 20000])
     ap.add_argument("--serve-seconds", type=float, default=2.0)

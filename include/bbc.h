@@ -136,11 +136,11 @@ bbc_status bbc_count_async(bbc_graph *g, uint64_t *totals_dev, uint64_t *per_u,
 /*
  * bbc_count_noalloc -- bbc_count's global totals for a prepared graph, without any
  * device or host allocation. The paper has no counterpart; this entry point exists for
- * callers that cannot allocate at the time they count: code running while a stream is
- * being captured into a CUDA graph (an allocation would be recorded into, or break,
- * the capture), latency-critical loops that must not pay for an allocation's implicit
- * synchronisation, and processes whose device memory is already reserved in full by
- * another framework's allocator, where any new allocation fails.
+ * callers that cannot allocate at the time they count: processes whose device memory is
+ * already reserved in full by another framework's caching allocator (any new allocation
+ * fails there), latency-critical loops that must not pay for the implicit device-wide
+ * synchronisation of cudaMalloc / cudaFree, and hosts that cap a library's device memory
+ * at what it holds once loaded.
  *
  *   g           a graph from bbc_prepare (its device layout is the input; unchanged).
  *   totals_dev  device uint64[2], caller-owned: receives {balanced, unbalanced}.
@@ -154,6 +154,10 @@ bbc_status bbc_count_async(bbc_graph *g, uint64_t *totals_dev, uint64_t *per_u,
  * with that device current); make that first call before any stream capture. All calls
  * share the one array and each clears what must start at zero, so calls that overlap on
  * the GPU (different streams, or threads without ordering) race and give wrong results.
+ * Work is one item per anchor covering all of its endpoint tiles (no split of heavy
+ * anchors across blocks, unlike bbc_count), so on graphs with a few dominant hubs the
+ * call can take much longer than bbc_count: the hubs' tiles run one after another on
+ * one block.
  */
 bbc_status bbc_count_noalloc(const bbc_graph *g, uint64_t *totals_dev, void *cuda_stream);
 
@@ -260,8 +264,63 @@ bbc_status bbc_wait(bbc_server *s, uint64_t ticket, int64_t timeout_us, uint64_t
 bbc_status bbc_server_stats(bbc_server *s, uint64_t *completed, double *p50_us,
                             double *p99_us, double *mean_us);
 
+/*
+ * Counters of a server since its creation, for capacity reports (not part of the
+ * counting). All times are host wall-clock microseconds except tick_gpu_us, the summed
+ * device time of the ticks' counting launches (CUDA events on the server's stream).
+ */
+typedef struct bbc_server_counters {
+    uint64_t submitted;           /* requests accepted by bbc_submit */
+    uint64_t admitted;            /* requests whose reservation was taken */
+    uint64_t completed;           /* requests finished, with any status */
+    uint64_t admitted_after_wait; /* admitted requests that had found the budget full (or
+                                     an earlier request still waiting) and were admitted
+                                     only after another request released its memory */
+    uint64_t queued_now;          /* requests waiting for admission now */
+    uint64_t max_queued;          /* most requests waiting for admission at once */
+    uint64_t max_resident;        /* most admitted, unfinished requests at once */
+    uint64_t ticks;               /* counting launches of the tick loop */
+    size_t budget_bytes;
+    size_t reserved_bytes;        /* reserved by admitted, unfinished requests now */
+    size_t peak_reserved_bytes;   /* the most ever reserved at once (<= budget_bytes) */
+    double tick_wall_us;          /* time the tick thread spent inside ticks */
+    double tick_gpu_us;           /* device time of the ticks' counting kernels */
+    double prep_wall_us;          /* summed preparation time over the preparation threads */
+    double elapsed_us;            /* since bbc_server_create */
+} bbc_server_counters;
+
+bbc_status bbc_server_counters_get(bbc_server *s, bbc_server_counters *out);
+
+/* What happened to one finished request (BBC_E_NOT_READY while it is in flight). */
+typedef struct bbc_request_info {
+    int32_t status;               /* the request's own status */
+    int32_t ticks;                /* counting launches it took part in */
+    int64_t n_edges;
+    uint64_t wedges;              /* W of its graph (0 if preparation failed) */
+    size_t reserved_bytes;        /* its reservation */
+    int32_t waited_for_memory;    /* 1: it was not admitted at submission */
+    int32_t pad;
+    double latency_us;            /* submission to completion */
+    double queued_us;             /* submission to admission */
+    double prepare_us;            /* admission to the end of its preparation */
+    double count_us;              /* end of preparation to completion */
+    double tick_gpu_us;           /* device time of the ticks it was in (shared with the
+                                     other requests of those ticks) */
+    double submit_us;             /* its submission, in microseconds after bbc_server_create */
+} bbc_request_info;
+
+bbc_status bbc_server_request_info(bbc_server *s, uint64_t ticket, bbc_request_info *out);
+
 /* Stops the loop; requests still queued finish with BBC_E_CANCELLED. */
 void bbc_server_destroy(bbc_server *s);
+
+/*
+ * Device memory of the library's stream-ordered pool on the current device: *used is
+ * what the library's live allocations hold now, *used_high the most they held at once
+ * since the process started or since the last call with reset_high != 0 (which resets it
+ * to the current use). Either pointer may be NULL.
+ */
+bbc_status bbc_memory_usage(size_t *used, size_t *used_high, int32_t reset_high);
 
 /*
  * bbc_count_delta -- the exact change of the counts when a batch of edge updates is

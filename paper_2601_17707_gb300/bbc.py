@@ -41,7 +41,7 @@ EXPORTS = (
     "bbc_cost_model_num_params", "bbc_cost_model_get_params", "bbc_cost_model_set_params",
     "bbc_cost_model_loss_grad", "bbc_cost_model_fit", "bbc_cost_model_predict", "bbc_item_features",
     "bbc_item_cycles", "bbc_cost_model_order", "bbc_count_delta", "bbc_graph_work",
-    "bbc_item_anchors",
+    "bbc_item_anchors", "bbc_server_counters_get", "bbc_server_request_info", "bbc_memory_usage",
 )
 
 MOTIF_SIGN_CLASSES = 1
@@ -56,6 +56,33 @@ class BBCError(RuntimeError):
 
 class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+class ServerCounters(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+        ("admitted_after_wait", ctypes.c_uint64), ("queued_now", ctypes.c_uint64),
+        ("max_queued", ctypes.c_uint64), ("max_resident", ctypes.c_uint64), ("ticks", ctypes.c_uint64),
+        ("budget_bytes", ctypes.c_size_t), ("reserved_bytes", ctypes.c_size_t),
+        ("peak_reserved_bytes", ctypes.c_size_t), ("tick_wall_us", ctypes.c_double),
+        ("tick_gpu_us", ctypes.c_double), ("prep_wall_us", ctypes.c_double), ("elapsed_us", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32), ("ticks", ctypes.c_int32), ("n_edges", ctypes.c_int64),
+        ("wedges", ctypes.c_uint64), ("reserved_bytes", ctypes.c_size_t),
+        ("waited_for_memory", ctypes.c_int32), ("pad", ctypes.c_int32),
+        ("latency_us", ctypes.c_double), ("queued_us", ctypes.c_double), ("prepare_us", ctypes.c_double),
+        ("count_us", ctypes.c_double), ("tick_gpu_us", ctypes.c_double), ("submit_us", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
 class Tuning(ctypes.Structure):
@@ -108,6 +135,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
                                  ctypes.c_int),
             "bbc_server_destroy": ([vp], None),
+            "bbc_server_counters_get": ([vp, ctypes.POINTER(ServerCounters)], ctypes.c_int),
+            "bbc_server_request_info": ([vp, ctypes.c_uint64, ctypes.POINTER(RequestInfo)], ctypes.c_int),
+            "bbc_memory_usage": ([ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t), i32],
+                                 ctypes.c_int),
             "bbc_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "bbc_launch_count": ([], ctypes.c_ulonglong),
             "bbc_profile_start": ([], ctypes.c_int),
@@ -155,6 +186,16 @@ def profile_stop() -> dict:
     check(load().bbc_profile_stop(arr, 8, ctypes.byref(n)), "bbc_profile_stop")
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
             for i in range(min(n.value, 8))}
+
+
+def memory_usage(reset_high: bool = False) -> tuple[int, int]:
+    """(bytes the library's device pool holds now, the most it held at once since the
+    last reset) on the current device."""
+    used = ctypes.c_size_t()
+    high = ctypes.c_size_t()
+    check(load().bbc_memory_usage(ctypes.byref(used), ctypes.byref(high), int(bool(reset_high))),
+          "bbc_memory_usage")
+    return int(used.value), int(high.value)
 
 
 def last_error() -> str:
@@ -452,6 +493,20 @@ class Server:
         check(load().bbc_server_stats(self._h, ctypes.byref(c), ctypes.byref(p50), ctypes.byref(p99),
                                       ctypes.byref(mean)), "bbc_server_stats")
         return {"completed": c.value, "p50_us": p50.value, "p99_us": p99.value, "mean_us": mean.value}
+
+    def counters(self) -> dict:
+        c = ServerCounters()
+        check(load().bbc_server_counters_get(self._h, ctypes.byref(c)), "bbc_server_counters_get")
+        return c.as_dict()
+
+    def request_info(self, ticket: int) -> dict:
+        """What happened to one finished request (None while it is in flight)."""
+        q = RequestInfo()
+        st = load().bbc_server_request_info(self._h, ticket, ctypes.byref(q))
+        if st == 11:
+            return None
+        check(st, "bbc_server_request_info")
+        return q.as_dict()
 
     def close(self) -> None:
         if self._h.value:

@@ -553,6 +553,24 @@ bbc_status bbc_profile_stop(bbc_kernel_time *out, int32_t capacity, int32_t *cou
     return st;
 }
 
+bbc_status bbc_memory_usage(size_t *used, size_t *used_high, int32_t reset_high) {
+    PoolEntry *e = device_entry();
+    if (!e) {
+        set_error("bbc_memory_usage: no device memory pool");
+        return BBC_E_CUDA;
+    }
+    uint64_t cur = 0, high = 0;
+    BBC_CUDA_TRY(cudaMemPoolGetAttribute(e->pool, cudaMemPoolAttrUsedMemCurrent, &cur));
+    BBC_CUDA_TRY(cudaMemPoolGetAttribute(e->pool, cudaMemPoolAttrUsedMemHigh, &high));
+    if (used) *used = (size_t)cur;
+    if (used_high) *used_high = (size_t)high;
+    if (reset_high) {
+        uint64_t zero = 0;
+        BBC_CUDA_TRY(cudaMemPoolSetAttribute(e->pool, cudaMemPoolAttrUsedMemHigh, &zero));
+    }
+    return BBC_OK;
+}
+
 bbc_status bbc_graph_info(const bbc_graph *g, int32_t *side, uint64_t *wedges,
                           size_t *device_bytes, int64_t *n_edges) {
     if (!g) return BBC_E_INVALID_ARG;

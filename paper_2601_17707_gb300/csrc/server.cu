@@ -43,9 +43,13 @@ struct Request {
     bbc_graph *g = nullptr;
     int32_t tile_done = 0, warp_done = 0, wt_done = 0, gt_done = 0;
     bool done = false;
+    bool waited = false;         // found the budget full at submission
     bbc_status status = BBC_OK;
     uint64_t balanced = 0;
-    Clock::time_point t_submit, t_done;
+    uint64_t wedges = 0;         // W of the prepared graph
+    int32_t ticks = 0;           // counting launches this request took part in
+    double gpu_us = 0;           // device time of those launches (shared with the others)
+    Clock::time_point t_submit, t_admit, t_ready, t_done;
 };
 
 // Device memory a request may hold at its peak (preparation temporaries included).
@@ -86,6 +90,13 @@ struct bbc_server {
     bool stop = false;
     std::thread worker;
     std::vector<double> latencies_us;
+    // counters (bbc_server_counters_get)
+    std::chrono::steady_clock::time_point t_created;
+    uint64_t n_submitted = 0, n_admitted = 0, n_completed = 0, n_waited = 0;
+    uint64_t n_ticks = 0, max_queue = 0, max_resident = 0;
+    double tick_wall_us = 0, tick_gpu_us = 0, prep_wall_us = 0;
+    size_t peak_reserved = 0;
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     // tick buffers (grown as needed)
     bbc::DevGraph *dgraphs = nullptr;
     size_t dgraphs_cap = 0;
@@ -112,6 +123,7 @@ void finish_locked(bbc_server *S, Request *r, bbc_status st, uint64_t balanced) 
     r->balanced = balanced;
     r->done = true;
     r->t_done = Clock::now();
+    S->n_completed++;
     r->u = {};
     r->v = {};
     r->s = {};
@@ -127,9 +139,20 @@ void admit_locked(bbc_server *S) {
         Request *r = S->queue.front();
         S->queue.pop_front();
         S->reserved += r->reserve;
+        S->peak_reserved = std::max(S->peak_reserved, S->reserved);
+        S->n_admitted++;
+        if (r->waited) S->n_waited++;
+        r->t_admit = Clock::now();
         S->to_prepare.push_back(r);
         any = true;
     }
+    if (!S->queue.empty()) {
+        // whoever is still queued now waits for memory to be released
+        for (Request *q : S->queue) q->waited = true;
+    }
+    const uint64_t resident = (uint64_t)(S->to_prepare.size() + S->ready.size() + S->active.size()) +
+                              (uint64_t)S->preparing;
+    S->max_resident = std::max(S->max_resident, resident);
     if (any) S->cv_prep.notify_all();
 }
 
@@ -150,6 +173,7 @@ void prep_main(bbc_server *S) {
             S->to_prepare.pop_front();
             S->preparing++;
         }
+        const Clock::time_point t0 = Clock::now();
         bbc_graph *g = nullptr;
         bbc_status s = prepare_graph(r->n_u, r->n_v, r->n_edges, r->u.data(), r->v.data(),
                                      r->s.data(), 0u, st, &g);
@@ -161,6 +185,8 @@ void prep_main(bbc_server *S) {
         }
         std::lock_guard<std::mutex> lk(S->mu);
         S->preparing--;
+        r->t_ready = Clock::now();
+        S->prep_wall_us += std::chrono::duration<double, std::micro>(r->t_ready - t0).count();
         if (s != BBC_OK) {
             if (g) release_graph(g, st);
             S->reserved -= r->reserve;
@@ -169,6 +195,7 @@ void prep_main(bbc_server *S) {
             S->cv_done.notify_all();
         } else {
             r->g = g;
+            r->wedges = g->wedges;
             r->u = {};
             r->v = {};
             r->s = {};
@@ -245,7 +272,9 @@ bbc_status run_tick(bbc_server *S, std::vector<Request *> &act) {
     L.n_gt_items = (int32_t)ngr;
     L.queue = S->queue_state;
     L.tuning = S->tuning;
+    BBC_CUDA_TRY(cudaEventRecord(S->ev_a, st));
     BBC_TRY(launch_count(L, st));
+    BBC_CUDA_TRY(cudaEventRecord(S->ev_b, st));
     for (size_t i = 0; i < n; ++i) {
         act[i]->tile_done += take_t[i];
         act[i]->warp_done += take_h[i];
@@ -257,6 +286,17 @@ bbc_status run_tick(bbc_server *S, std::vector<Request *> &act) {
     QueueState qs{};
     BBC_CUDA_TRY(cudaMemcpyAsync(&qs, S->queue_state, sizeof qs, cudaMemcpyDeviceToHost, st));
     BBC_CUDA_TRY(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    BBC_CUDA_TRY(cudaEventElapsedTime(&ms, S->ev_a, S->ev_b));
+    for (size_t i = 0; i < n; ++i) {
+        act[i]->ticks++;
+        act[i]->gpu_us += 1e3 * (double)ms;
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->n_ticks++;
+        S->tick_gpu_us += 1e3 * (double)ms;
+    }
     if (qs.error) {
         set_error("serving tick: counting kernel reported an internal inconsistency");
         return BBC_E_CUDA;
@@ -277,8 +317,10 @@ void worker_main(bbc_server *S) {
             act = S->active;
         }
         if (act.empty()) continue;
+        const Clock::time_point t0 = Clock::now();
         const bbc_status st = run_tick(S, act);
         std::lock_guard<std::mutex> lk(S->mu);
+        S->tick_wall_us += std::chrono::duration<double, std::micro>(Clock::now() - t0).count();
         std::vector<Request *> still;
         for (size_t i = 0; i < act.size(); ++i) {
             Request *r = act[i];
@@ -317,8 +359,13 @@ bbc_status bbc_server_create(size_t device_budget_bytes, const bbc_tuning *tunin
         S->tuning = resolve_tuning(tuning, device_sm_count());
         if (S->tuning.split_wedges == 0) S->tuning.split_wedges = (long long)1 << 26;
         cudaGetDevice(&S->device);
+        S->t_created = Clock::now();
         cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreate(&S->ev_a);
+        if (e == cudaSuccess) e = cudaEventCreate(&S->ev_b);
         if (e != cudaSuccess) {
+            if (S->ev_a) cudaEventDestroy(S->ev_a);
+            if (S->stream) cudaStreamDestroy(S->stream);
             delete S;
             return cuda_fail(e, "bbc_server_create stream");
         }
@@ -361,8 +408,10 @@ bbc_status bbc_submit(bbc_server *S, int32_t n_u, int32_t n_v, int64_t n_edges, 
         r->ticket = S->next_ticket++;
         S->all[r->ticket] = r;
         S->queue.push_back(r);
+        S->n_submitted++;
         *ticket = r->ticket;
         admit_locked(S);
+        S->max_queue = std::max<uint64_t>(S->max_queue, S->queue.size());
         return BBC_OK;
     } catch (...) {
         set_error("bbc_submit: host allocation failed");
@@ -429,6 +478,67 @@ bbc_status bbc_server_stats(bbc_server *S, uint64_t *completed, double *p50_us, 
     return BBC_OK;
 }
 
+bbc_status bbc_server_counters_get(bbc_server *S, bbc_server_counters *out) {
+    if (!S || !out) {
+        set_error("bbc_server_counters_get: NULL argument");
+        return BBC_E_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    bbc_server_counters c{};
+    c.submitted = S->n_submitted;
+    c.admitted = S->n_admitted;
+    c.completed = S->n_completed;
+    c.admitted_after_wait = S->n_waited;
+    c.queued_now = S->queue.size();
+    c.max_queued = S->max_queue;
+    c.max_resident = S->max_resident;
+    c.ticks = S->n_ticks;
+    c.budget_bytes = S->budget;
+    c.reserved_bytes = S->reserved;
+    c.peak_reserved_bytes = S->peak_reserved;
+    c.tick_wall_us = S->tick_wall_us;
+    c.tick_gpu_us = S->tick_gpu_us;
+    c.prep_wall_us = S->prep_wall_us;
+    c.elapsed_us = std::chrono::duration<double, std::micro>(Clock::now() - S->t_created).count();
+    *out = c;
+    return BBC_OK;
+}
+
+bbc_status bbc_server_request_info(bbc_server *S, uint64_t ticket, bbc_request_info *out) {
+    if (!S || !out) {
+        set_error("bbc_server_request_info: NULL argument");
+        return BBC_E_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end()) {
+        set_error("bbc_server_request_info: unknown ticket");
+        return BBC_E_INVALID_ARG;
+    }
+    const Request *r = it->second;
+    if (!r->done) return BBC_E_NOT_READY;
+    auto us = [](Clock::time_point a, Clock::time_point b) {
+        return std::chrono::duration<double, std::micro>(b - a).count();
+    };
+    bbc_request_info q{};
+    q.status = r->status;
+    q.n_edges = r->n_edges;
+    q.wedges = r->wedges;
+    q.reserved_bytes = r->reserve;
+    q.ticks = r->ticks;
+    q.waited_for_memory = r->waited ? 1 : 0;
+    const bool admitted = r->t_admit.time_since_epoch().count() != 0;
+    const bool prepared = r->t_ready.time_since_epoch().count() != 0;
+    q.latency_us = us(r->t_submit, r->t_done);
+    q.queued_us = admitted ? us(r->t_submit, r->t_admit) : q.latency_us;
+    q.prepare_us = admitted && prepared ? us(r->t_admit, r->t_ready) : 0.0;
+    q.count_us = prepared ? us(r->t_ready, r->t_done) : 0.0;
+    q.tick_gpu_us = r->gpu_us;
+    q.submit_us = us(S->t_created, r->t_submit);
+    *out = q;
+    return BBC_OK;
+}
+
 void bbc_server_destroy(bbc_server *S) {
     if (!S) return;
     {
@@ -463,6 +573,8 @@ void bbc_server_destroy(bbc_server *S) {
         if (p) dev_free(p, S->stream);
     cudaStreamSynchronize(S->stream);
     if (S->host_totals) cudaFreeHost(S->host_totals);
+    cudaEventDestroy(S->ev_a);
+    cudaEventDestroy(S->ev_b);
     cudaStreamDestroy(S->stream);
     cudaSetDevice(prev);
     for (auto &kv : S->all) delete kv.second;

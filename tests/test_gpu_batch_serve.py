@@ -144,6 +144,71 @@ def test_serving_budget_and_bounded_waits(gpu_lib):
         srv.close()
 
 
+def test_serving_admits_requests_as_memory_frees(gpu_lib):
+    """A budget that holds two requests' reservations and 40 requests submitted at once:
+    the rest queue, each is admitted only after an earlier one released its memory, the
+    reservations never exceed the budget, and every count equals the oracle's."""
+    gs = [synth.uniform_graph(1500, 2500, 30_000, 0.7, seed=100 + i) for i in range(40)]
+    want = [oracle.count(g, threads=2, per_vertex=False).balanced for g in gs]
+    probe = bbc.Server(8 << 30)
+    try:
+        t = probe.submit(gs[0])
+        assert probe.wait(t, 60.0) == want[0]
+        reserve = probe.request_info(t)["reserved_bytes"]
+    finally:
+        probe.close()
+    budget = int(2.5 * reserve)
+    srv = bbc.Server(budget)
+    try:
+        tickets = [srv.submit(g) for g in gs]
+        got = [srv.wait(t, timeout_s=120.0) for t in tickets]
+        assert got == want
+        c = srv.counters()
+        assert c["submitted"] == c["admitted"] == c["completed"] == len(gs)
+        assert c["peak_reserved_bytes"] <= budget == c["budget_bytes"]
+        assert c["reserved_bytes"] == 0 and c["queued_now"] == 0
+        assert c["max_resident"] <= 2
+        assert c["max_queued"] >= len(gs) - 2
+        assert c["admitted_after_wait"] >= len(gs) - 2
+        info = [srv.request_info(t) for t in tickets]
+        admit = [q["submit_us"] + q["queued_us"] for q in info]
+        done = [q["submit_us"] + q["latency_us"] for q in info]
+        for k, q in enumerate(info):
+            assert q["status"] == 0 and q["reserved_bytes"] == reserve
+            if q["waited_for_memory"]:
+                # admitted no earlier than some other request's completion
+                assert any(done[j] <= admit[k] + 1.0 for j in range(len(gs)) if j != k), k
+        # at no instant were more than two requests admitted and unfinished
+        events = sorted([(a, 1) for a in admit] + [(d, -1) for d in done], key=lambda e: (e[0], e[1]))
+        live = peak = 0
+        for _, step in events:
+            live += step
+            peak = max(peak, live)
+        assert peak <= 2
+    finally:
+        srv.close()
+
+
+def test_serving_reservation_covers_measured_peak(gpu_lib):
+    """The device memory one request actually reaches at its peak (the library pool's
+    high-water mark, preparation temporaries and tick buffers included) stays within the
+    reservation that admission charges for it."""
+    g = synth.powerlaw_1m_200k(seed=11, scale=0.05)
+    srv = bbc.Server(8 << 30)
+    try:
+        warm = srv.submit(synth.uniform_graph(50, 60, 200, 0.5, seed=1))
+        srv.wait(warm, 60.0)
+        used0, _ = bbc.memory_usage(reset_high=True)
+        t = srv.submit(g)
+        assert srv.wait(t, 120.0) == oracle.count(g, threads=8, per_vertex=False).balanced
+        _, high = bbc.memory_usage()
+        q = srv.request_info(t)
+        assert 0 < high - used0 <= q["reserved_bytes"], (high - used0, q["reserved_bytes"])
+        assert q["wedges"] > 0 and q["ticks"] >= 1 and q["count_us"] > 0
+    finally:
+        srv.close()
+
+
 def test_serving_shutdown_cancels_queued_requests(gpu_lib):
     srv = bbc.Server(8 << 30)
     gs = small_batch(40, seed=12)
