@@ -202,7 +202,7 @@ Tuning resolve_tuning(const bbc_tuning *t, int sm_count) {
     // of blocks_per_sm resident blocks (228 KB per SM, 1 KB reserved per block, minus
     // the kernel's static shared memory); hash tables hold at most 512 wedges
     const int per_block = (228 * 1024) / r.blocks_per_sm - 1024 - tile_static_smem_bytes();
-    const int cap = std::min(per_block, 227 * 1024 - tile_static_smem_bytes()) / 4;
+    const int cap = std::min(per_block, 227 * 1024 - tile_static_smem_bytes()) / 4 - kTileSlackWords;
     if (r.tile_words == 0 || r.tile_words > cap) r.tile_words = cap;
     if (r.tile_words < 1024) r.tile_words = 1024;
     r.tile_words &= ~7;

@@ -65,6 +65,11 @@ __host__ __device__ inline int width_for_bound(unsigned long long bound) {
 __host__ __device__ constexpr uint32_t tile_endpoints(int cw, uint32_t tile_words) {
     return cw == 0 ? tile_words * 2 : (cw == 1 ? tile_words : tile_words / 2);
 }
+// Words the tile kernel allocates past tile_words: a tile of 8-bit counters whose first
+// endpoint is odd starts one endpoint early (its words hold an even and an odd endpoint),
+// and the epilogue reads whole 16-byte groups.
+constexpr int kTileSlackWords = 4;
+
 struct VarTile {
     uint32_t lo, hi;   // endpoint ranks [lo, hi)
     int cw;

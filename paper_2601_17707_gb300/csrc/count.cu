@@ -302,11 +302,85 @@ struct TileCounter {
     }
     // a C -> S entry x (endpoint rank | sign << 31) reached through an anchor edge of
     // sign bit sg: the wedge is symmetric (t = 0) or asymmetric (t = 1)
+    __device__ static __forceinline__ uint32_t sign_key(uint32_t sg) { return sg; }
     __device__ __forceinline__ void bump_entry(uint32_t x, uint32_t sg) const {
         bump(x & kIdMask, (x ^ sg) >> 31);
     }
-    __device__ __forceinline__ uint32_t peek_entry(uint32_t x, uint32_t sg) const {
+    __device__ __forceinline__ uint32_t count_entry(uint32_t x, uint32_t sg) const {
         return peek(x & kIdMask, (x ^ sg) >> 31);
+    }
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void smem_red_add(uint32_t a, uint32_t v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v));
+}
+__device__ __forceinline__ uint32_t smem_load(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t rotl(uint32_t x, int k) { return __funnelshift_l(x, x, k); }
+
+// The block tile of k_tile, the same counters as TileCounter's but addressed through
+// 32-bit shared-memory addresses with the tile's origin folded into one base, so that a
+// C -> S entry x (endpoint rank w | sign << 31) reaches its counter in a few integer
+// operations. Byte offset of the counter of endpoint w and wedge type t:
+//   CW 0: 2 (w - org) + t with org = lo rounded down to even (a word holds the counters
+//         of an even and an odd endpoint: bytes p0, n0, p1, n1), so the word is
+//         (base + 2x) & ~3 and the byte within it 2 (w & 1) + t, whose shift 16 (w & 1) +
+//         8 t is bits 4 and 3 of x rotated left by 4 (x's low bit and sign bit) with the
+//         anchor edge's sign xor-ed in;
+//   CW 1: 4 (w - org) + 2 t with org = lo: the word is base + 4x, the shift 16 t;
+//   CW 2: 8 (w - org) + 4 t with org = lo: the word is base + 4 * rotl(x ^ sg, 1), since
+//         that rotation is 2 w + t.
+// All address arithmetic is modulo 2^32, so bits shifted out of x (its sign, and high
+// rank bits) only add multiples of 2^32 and the address stays exact. A tile whose lo is
+// odd uses one word beyond tile_words with 8-bit counters (the kernel allocates it).
+template <int CW>
+struct BlockTile {
+    uint32_t base;
+    __device__ static __forceinline__ uint32_t origin(uint32_t lo) { return CW == 0 ? (lo & ~1u) : lo; }
+    __device__ __forceinline__ BlockTile(const uint32_t *tile, uint32_t lo) {
+        const uint32_t a = smem_addr(tile), o = origin(lo);
+        base = a - (CW == 0 ? 2u : (CW == 1 ? 4u : 8u)) * o;
+    }
+    // the anchor edge's sign bit sg where the entry's sign bit lands in shift()/word()
+    __device__ static __forceinline__ uint32_t sign_key(uint32_t sg) {
+        return CW == 0 ? sg >> 28 : (CW == 1 ? sg >> 27 : sg);
+    }
+    __device__ __forceinline__ uint32_t word(uint32_t x, uint32_t sk) const {
+        if (CW == 0) return (base + 2u * x) & ~3u;
+        if (CW == 1) return base + 4u * x;
+        return base + 4u * rotl(x ^ sk, 1);
+    }
+    __device__ __forceinline__ uint32_t shift(uint32_t x, uint32_t sk) const {
+        if (CW == 0) return (rotl(x, 4) ^ sk) & 24u;
+        if (CW == 1) return (rotl(x, 5) ^ sk) & 16u;
+        return 0u;
+    }
+    __device__ __forceinline__ void bump_entry(uint32_t x, uint32_t sk) const {
+        smem_red_add(word(x, sk), CW == 2 ? 1u : 1u << shift(x, sk));
+    }
+    // the counter of the wedge's endpoint and type (its full count, once the tile is done)
+    __device__ __forceinline__ uint32_t count_entry(uint32_t x, uint32_t sk) const {
+        const uint32_t v = smem_load(word(x, sk));
+        if (CW == 0) return (uint32_t)__dp4a(v, 1u << shift(x, sk), 0u);
+        if (CW == 1) return (v >> shift(x, sk)) & 0xffffu;
+        return v;
+    }
+    // acc plus that counter (8-bit counters: one dp4a picks the byte and adds it)
+    __device__ __forceinline__ void add_count(uint32_t x, uint32_t sk, uint32_t &acc) const {
+        const uint32_t v = smem_load(word(x, sk));
+        if (CW == 0)
+            acc = (uint32_t)__dp4a(v, 1u << shift(x, sk), acc);
+        else
+            acc += (v >> shift(x, sk)) & 0xffffu;
+    }
+    __device__ __forceinline__ void add_count(uint32_t x, uint32_t sk, unsigned long long &acc) const {
+        acc += count_entry(x, sk);
     }
 };
 
@@ -328,7 +402,10 @@ struct ClassCounter {
         else
             atomicAdd(tile + 4 * e + kind, 1u);
     }
-    __device__ __forceinline__ uint32_t peek_entry(uint32_t, uint32_t) const { return 1u; }
+    __device__ static __forceinline__ uint32_t sign_key(uint32_t sg) { return sg; }
+    __device__ __forceinline__ uint32_t count_entry(uint32_t, uint32_t) const { return 1u; }
+    template <class A>
+    __device__ __forceinline__ void add_count(uint32_t, uint32_t, A &acc) const { acc += 1u; }
     __device__ __forceinline__ void read(uint32_t e, uint32_t &pp, uint32_t &nn, uint32_t &a) const {
         if (CW == 0) {
             const uint32_t v = tile[e];
@@ -411,19 +488,6 @@ __device__ __forceinline__ unsigned long long block_exclusive_scan_u64(unsigned 
     return wsum[warp] + inc - x;
 }
 
-// index of the last entry <= k in the non-decreasing p[0..kChunk] (p[0] == 0 <= k)
-__device__ __forceinline__ int last_le(const uint32_t *p, uint32_t k) {
-    int lo = 0, hi = kChunk;  // invariant: p[lo] <= k < p[hi + 1] or hi == kChunk
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (p[mid] <= k)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
 // Per-wedge work. MODE 1 sums (count - 1); with 8- and 16-bit counters a thread's or a
 // piece's sum stays far below 2^32 (at most 1,024 wedges of count <= 65,535), so it is
 // kept in 32 bits; 32-bit counters use 64-bit sums.
@@ -438,13 +502,20 @@ __device__ __forceinline__ uint32_t warp_sum32(uint32_t x) {
 __device__ __forceinline__ unsigned long long warp_sum_acc(unsigned long long x) { return warp_sum(x); }
 __device__ __forceinline__ uint32_t warp_sum_acc(uint32_t x) { return warp_sum32(x); }
 
+// One wedge given by its C -> S entry x and the counter's sign key of the anchor edge:
+// MODE 0 bumps its counter; MODE 1 adds the counter's value to acc (the caller subtracts
+// one per wedge afterwards).
 template <int MODE, int CW, class Ctr>
-__device__ __forceinline__ void wedge(const Ctr &ctr, uint32_t x, uint32_t sg, Acc<CW> &acc) {
-    if (MODE == 0)
-        ctr.bump_entry(x, sg);
+__device__ __forceinline__ void wedge(const Ctr &ctr, uint32_t x, uint32_t sk, Acc<CW> &acc) {
+    if constexpr (MODE == 0)
+        ctr.bump_entry(x, sk);
     else
-        acc += ctr.peek_entry(x, sg) - 1u;
+        ctr.add_count(x, sk, acc);
 }
+
+// Sum over a warp of a per-lane accumulator (one redux instruction for 32 bits).
+__device__ __forceinline__ uint32_t warp_total(uint32_t x) { return __reduce_add_sync(kFull, x); }
+__device__ __forceinline__ unsigned long long warp_total(unsigned long long x) { return warp_sum(x); }
 
 // First index of row[b, lim) whose rank is >= key (the row is sorted by rank), found by
 // galloping from b: about 2 log2 of the distance instead of log2 of the row length.
@@ -595,7 +666,9 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
                     Acc<CW> v = 0;
                     if (j >= 0) {
                         meta = cs.smeta[j];
-                        wedge<MODE, CW>(ctr, __ldg(rowC + (uint32_t)(cs.sbase[j] + k)), meta & kSignBit, v);
+                        wedge<MODE, CW>(ctr, __ldg(rowC + (uint32_t)(cs.sbase[j] + k)),
+                                        Ctr::sign_key(meta & kSignBit), v);
+                        if (MODE == 1) v -= 1u;
                     }
                     j0 += __popc(m) + (at32 ? 1 : 0);
                     if (MODE == 1) {
@@ -613,21 +686,31 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
                 }
             }
         }
-        // long slices: pieces pulled by warps
+        // long slices: pieces pulled by warps. Pieces are handed out in increasing order,
+        // so a warp finds the slice of its next piece by scanning forward from the slice
+        // of its last one, 32 prefix entries per step.
         if (NP) {
+            int jw = 0;
             for (;;) {
                 uint32_t pc = 0;
                 if (lane == 0) pc = (uint32_t)atomicAdd(&cs.piece_ctr, 1);
                 pc = __shfl_sync(kFull, pc, 0);
                 if (pc >= NP) break;
-                const int j = last_le(cs.ppiece, pc);
+                for (;;) {
+                    const int idx = jw + 1 + lane;
+                    const uint32_t val = idx <= kChunk ? cs.ppiece[idx] : 0xffffffffu;
+                    const unsigned b = __ballot_sync(kFull, val <= pc);
+                    jw += __popc(b);
+                    if (b != kFull) break;
+                }
+                const int j = jw;
                 const uint32_t off = (pc - cs.ppiece[j]) * (uint32_t)kPiece;
                 const uint32_t n = min((uint32_t)kPiece, cs.len[j] - off);
                 const uint32_t s = cs.start[j] + off;
-                const uint32_t sg = cs.ent[j] & kSignBit;
+                const uint32_t sk = Ctr::sign_key(cs.ent[j] & kSignBit);
                 Acc<CW> acc = 0;
                 const uint32_t head = min(n, (4u - (s & 3u)) & 3u);
-                if ((uint32_t)lane < head) wedge<MODE, CW>(ctr, __ldg(rowC + s + lane), sg, acc);
+                if ((uint32_t)lane < head) wedge<MODE, CW>(ctr, __ldg(rowC + s + lane), sk, acc);
                 const uint32_t m4 = (n - head) >> 2;
                 const uint4 *v4 = reinterpret_cast<const uint4 *>(rowC + s + head);
                 // two 16-byte loads in flight per lane
@@ -635,22 +718,23 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
                     const uint4 xa = __ldg(v4 + q);
                     const bool has_b = q + 32 < m4;
                     const uint4 xb = has_b ? __ldg(v4 + q + 32) : make_uint4(0u, 0u, 0u, 0u);
-                    wedge<MODE, CW>(ctr, xa.x, sg, acc);
-                    wedge<MODE, CW>(ctr, xa.y, sg, acc);
-                    wedge<MODE, CW>(ctr, xa.z, sg, acc);
-                    wedge<MODE, CW>(ctr, xa.w, sg, acc);
+                    wedge<MODE, CW>(ctr, xa.x, sk, acc);
+                    wedge<MODE, CW>(ctr, xa.y, sk, acc);
+                    wedge<MODE, CW>(ctr, xa.z, sk, acc);
+                    wedge<MODE, CW>(ctr, xa.w, sk, acc);
                     if (has_b) {
-                        wedge<MODE, CW>(ctr, xb.x, sg, acc);
-                        wedge<MODE, CW>(ctr, xb.y, sg, acc);
-                        wedge<MODE, CW>(ctr, xb.z, sg, acc);
-                        wedge<MODE, CW>(ctr, xb.w, sg, acc);
+                        wedge<MODE, CW>(ctr, xb.x, sk, acc);
+                        wedge<MODE, CW>(ctr, xb.y, sk, acc);
+                        wedge<MODE, CW>(ctr, xb.z, sk, acc);
+                        wedge<MODE, CW>(ctr, xb.w, sk, acc);
                     }
                 }
                 const uint32_t rest = (n - head) & 3u;
-                if ((uint32_t)lane < rest) wedge<MODE, CW>(ctr, __ldg(rowC + s + head + 4 * m4 + lane), sg, acc);
+                if ((uint32_t)lane < rest) wedge<MODE, CW>(ctr, __ldg(rowC + s + head + 4 * m4 + lane), sk, acc);
                 if (MODE == 1) {
-                    acc = warp_sum_acc(acc);
-                    if (lane == 0 && acc) acc_add<CW>(cs, j, acc);
+                    // the piece's sum of counts minus one per wedge
+                    const Acc<CW> tot = warp_total(acc) - (Acc<CW>)n;
+                    if (lane == 0 && tot) acc_add<CW>(cs, j, tot);
                 }
             }
         }
@@ -674,8 +758,10 @@ __device__ __forceinline__ void pair_total(unsigned long long p, unsigned long l
     if (bS && f) red_add(bS + w, f);
 }
 
-// Reads, reduces and clears the tile of endpoints [lo, hi). Words past the last
-// endpoint in the final 16-byte group are never bumped and stay zero. With 8-bit
+// Reads, reduces and clears the tile of endpoints [lo, hi), lo being the tile's origin
+// (BlockTile::origin: with 8-bit counters an odd first endpoint leaves the word's first
+// slot, endpoint lo - 1, unbumped). Words past the last endpoint in the final 16-byte
+// group are never bumped and stay zero. With 8-bit
 // counters a word holds the bytes (p0, n0, p1, n1) of two endpoints, and
 // sum C(x, 2) = (sum x^2 - sum x) / 2 over its bytes, while p0 n0 + p1 n1 is half the
 // byte dot product of the word with its pair-swapped self: three dp4a per word.
@@ -751,10 +837,10 @@ __device__ void run_tile_item(const DevGraph &G, const TileItem &item, int tile_
         X.t = t;
         X.lo = X.range_lo + (uint32_t)t * ept;
         X.hi = min(X.lo + ept, X.range_hi);
-        const TileCounter<CW> ctr{tile, X.lo};
+        const BlockTile<CW> ctr(tile, X.lo);
         block_sweep<0, CW>(G, sb, se, X, ctr, cs, centre_carry);
         if (G.bC) block_sweep<1, CW>(G, sb, se, X, ctr, cs, centre_carry);
-        tile_epilogue<CW>(tile, X.lo, X.hi, G.bS, bal, unb);
+        tile_epilogue<CW>(tile, BlockTile<CW>::origin(X.lo), X.hi, G.bS, bal, unb);
         __syncthreads();
     }
     if (centre_carry) red_add(G.bC + (cs.ent[threadIdx.x] & kIdMask), centre_carry);
@@ -766,10 +852,10 @@ template <int CW>
 __device__ void tile_pass(const DevGraph &G, int64_t sb, int64_t se, const SweepCtx &X, uint32_t *tile,
                           ChunkSmem &cs, unsigned long long &centre_carry, unsigned long long &bal,
                           unsigned long long &unb) {
-    const TileCounter<CW> ctr{tile, X.lo};
+    const BlockTile<CW> ctr(tile, X.lo);
     block_sweep<0, CW>(G, sb, se, X, ctr, cs, centre_carry);
     if (G.bC) block_sweep<1, CW>(G, sb, se, X, ctr, cs, centre_carry);
-    tile_epilogue<CW>(tile, X.lo, X.hi, G.bS, bal, unb);
+    tile_epilogue<CW>(tile, BlockTile<CW>::origin(X.lo), X.hi, G.bS, bal, unb);
     __syncthreads();
 }
 
@@ -816,7 +902,7 @@ k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, 
     __shared__ int s_item;
     __shared__ unsigned long long s_red[2][kTileWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < tile_words; i += blockDim.x) tile[i] = 0;
+    for (int i = threadIdx.x; i < tile_words + kTileSlackWords; i += blockDim.x) tile[i] = 0;
     int next_static = blockIdx.x;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -1305,7 +1391,7 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
         // work-queue schedule: persistent blocks (no more than there are items); plain
         // schedule: one block per item
         const int grid = T.plain ? L.n_tile_items : std::min(L.n_tile_items, sms * T.blocks_per_sm);
-        k_tile<<<grid, kTileThreads, (size_t)T.tile_words * 4, st>>>(
+        k_tile<<<grid, kTileThreads, (size_t)(T.tile_words + kTileSlackWords) * 4, st>>>(
             L.graphs, L.tile_items, L.n_tile_items, &L.queue->tile_head, T.tile_words, T.plain,
             L.item_cycles);
         BBC_CUDA_TRY(cudaGetLastError());
@@ -1395,7 +1481,7 @@ bbc_status launch_tile_only(const DevGraph *graphs, const TileItem *items, int n
     BBC_TRY(configure_count_kernels());
     if (n_items <= 0) return BBC_OK;
     note_launch();
-    k_tile<<<blocks, kTileThreads, (size_t)tile_words * 4, st>>>(graphs, items, n_items, head,
+    k_tile<<<blocks, kTileThreads, (size_t)(tile_words + kTileSlackWords) * 4, st>>>(graphs, items, n_items, head,
                                                                  tile_words, 0, nullptr);
     BBC_CUDA_TRY(cudaGetLastError());
     return BBC_OK;
