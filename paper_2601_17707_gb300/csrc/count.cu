@@ -329,13 +329,15 @@ __device__ __forceinline__ uint32_t rotl(uint32_t x, int k) { return __funnelshi
 // C -> S entry x (endpoint rank w | sign << 31) reaches its counter in a few integer
 // operations. Byte offset of the counter of endpoint w and wedge type t:
 //   CW 0: 2 (w - org) + t with org = lo rounded down to even (a word holds the counters
-//         of an even and an odd endpoint: bytes p0, n0, p1, n1), so the word is
-//         (base + 2x) & ~3 and the byte within it 2 (w & 1) + t, whose shift 16 (w & 1) +
-//         8 t is bits 4 and 3 of x rotated left by 4 (x's low bit and sign bit) with the
-//         anchor edge's sign xor-ed in;
-//   CW 1: 4 (w - org) + 2 t with org = lo: the word is base + 4x, the shift 16 t;
-//   CW 2: 8 (w - org) + 4 t with org = lo: the word is base + 4 * rotl(x ^ sg, 1), since
-//         that rotation is 2 w + t.
+//         of an even and an odd endpoint: bytes p0, n0, p1, n1);
+//   CW 1: 4 (w - org) + 2 t with org = lo;
+//   CW 2: 8 (w - org) + 4 t with org = lo.
+// The counter's index 2 w + t is x xor the anchor edge's sign bit, rotated left by one,
+// so the centre pass loads each counter at its own width from base + width * that. The
+// count pass needs word-sized atomics: the word is (base + 2x) & ~3 (CW 0) or base + 4x
+// (CW 1), and the counter's bit offset in it, 16 (w & 1) + 8 t (CW 0) or 16 t (CW 1), is
+// x's low bit and sign bit brought into place by one rotation, with the anchor edge's
+// sign xor-ed in.
 // All address arithmetic is modulo 2^32, so bits shifted out of x (its sign, and high
 // rank bits) only add multiples of 2^32 and the address stays exact. A tile whose lo is
 // odd uses one word beyond tile_words with 8-bit counters (the kernel allocates it).
@@ -347,37 +349,43 @@ struct BlockTile {
         const uint32_t a = smem_addr(tile), o = origin(lo);
         base = a - (CW == 0 ? 2u : (CW == 1 ? 4u : 8u)) * o;
     }
-    // the anchor edge's sign bit sg where the entry's sign bit lands in shift()/word()
-    __device__ static __forceinline__ uint32_t sign_key(uint32_t sg) {
-        return CW == 0 ? sg >> 28 : (CW == 1 ? sg >> 27 : sg);
-    }
+    // the anchor edge's sign bit, as the slice's key
+    __device__ static __forceinline__ uint32_t sign_key(uint32_t sg) { return sg; }
+    // the word holding the counter (atomics are word-sized)
     __device__ __forceinline__ uint32_t word(uint32_t x, uint32_t sk) const {
         if (CW == 0) return (base + 2u * x) & ~3u;
         if (CW == 1) return base + 4u * x;
         return base + 4u * rotl(x ^ sk, 1);
     }
+    // the counter's bit offset within that word (the sign keys shifted into place are
+    // loop invariants of a slice)
     __device__ __forceinline__ uint32_t shift(uint32_t x, uint32_t sk) const {
-        if (CW == 0) return (rotl(x, 4) ^ sk) & 24u;
-        if (CW == 1) return (rotl(x, 5) ^ sk) & 16u;
+        if (CW == 0) return (rotl(x, 4) ^ (sk >> 28)) & 24u;
+        if (CW == 1) return (rotl(x, 5) ^ (sk >> 27)) & 16u;
         return 0u;
+    }
+    // the counter's own address: rotl(x ^ sg, 1) is 2 w + t, the counter's index
+    __device__ __forceinline__ uint32_t counter(uint32_t x, uint32_t sk) const {
+        return base + (CW == 0 ? 1u : (CW == 1 ? 2u : 4u)) * rotl(x ^ sk, 1);
     }
     __device__ __forceinline__ void bump_entry(uint32_t x, uint32_t sk) const {
         smem_red_add(word(x, sk), CW == 2 ? 1u : 1u << shift(x, sk));
     }
-    // the counter of the wedge's endpoint and type (its full count, once the tile is done)
+    // the counter of the wedge's endpoint and type (its full count, once the tile is done),
+    // read at its own width
     __device__ __forceinline__ uint32_t count_entry(uint32_t x, uint32_t sk) const {
-        const uint32_t v = smem_load(word(x, sk));
-        if (CW == 0) return (uint32_t)__dp4a(v, 1u << shift(x, sk), 0u);
-        if (CW == 1) return (v >> shift(x, sk)) & 0xffffu;
+        const uint32_t a = counter(x, sk);
+        uint32_t v;
+        if (CW == 0)
+            asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(a));
+        else if (CW == 1)
+            asm volatile("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(a));
+        else
+            v = smem_load(a);
         return v;
     }
-    // acc plus that counter (8-bit counters: one dp4a picks the byte and adds it)
     __device__ __forceinline__ void add_count(uint32_t x, uint32_t sk, uint32_t &acc) const {
-        const uint32_t v = smem_load(word(x, sk));
-        if (CW == 0)
-            acc = (uint32_t)__dp4a(v, 1u << shift(x, sk), acc);
-        else
-            acc += (v >> shift(x, sk)) & 0xffffu;
+        acc += count_entry(x, sk);
     }
     __device__ __forceinline__ void add_count(uint32_t x, uint32_t sk, unsigned long long &acc) const {
         acc += count_entry(x, sk);
@@ -433,9 +441,9 @@ __host__ __device__ constexpr uint32_t endpoints_per_tile(int cw, uint32_t tile_
 // Per-chunk bookkeeping of the block sweep: the slice of every centre of the chunk and
 // two prefix sums, over short-slice wedges and over long-slice pieces.
 struct ChunkSmem {
+    uint32_t ent[kChunk];
     uint32_t start[kChunk];
     uint32_t len[kChunk];
-    uint32_t ent[kChunk];
     uint32_t ppiece[kChunk + 1];
     // the chunk's non-empty short slices, compacted in centre order: concatenated start
     // (sP[nz] = ns, the chunk's short-wedge total), rowC index minus that start, and the
@@ -446,7 +454,7 @@ struct ChunkSmem {
     unsigned long long acc[kChunk];
     unsigned long long wsum[kTileWarps];
     uint32_t ns, nz;
-    int piece_ctr;
+    int piece_ctr, piece_ctr1;   // pieces handed out in the count and the centre pass
 };
 // index of the last entry <= k in the non-decreasing p[0..n] (p[0] == 0 <= k)
 __device__ __forceinline__ int last_le_n(const uint32_t *p, int n, uint32_t k) {
@@ -462,7 +470,7 @@ __device__ __forceinline__ int last_le_n(const uint32_t *p, int n, uint32_t k) {
 }
 
 __device__ __forceinline__ unsigned long long block_exclusive_scan_u64(unsigned long long x,
-                                                                      unsigned long long *total,
+                                                                      unsigned long long &total,
                                                                       unsigned long long *wsum) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long inc = x;
@@ -473,19 +481,16 @@ __device__ __forceinline__ unsigned long long block_exclusive_scan_u64(unsigned 
     }
     if (lane == 31) wsum[warp] = inc;
     __syncthreads();
-    if (warp == 0) {
-        const unsigned long long w = lane < kTileWarps ? wsum[lane] : 0ull;
-        unsigned long long wi = w;
+    // every warp scans the warp sums itself (no second barrier)
+    const unsigned long long w = lane < kTileWarps ? wsum[lane] : 0ull;
+    unsigned long long wi = w;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(kFull, wi, o);
-            if (lane >= o) wi += y;
-        }
-        if (lane < kTileWarps) wsum[lane] = wi - w;
-        if (lane == kTileWarps - 1) *total = wi;
+    for (int o = 1; o < kTileWarps; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, wi, o);
+        if (lane >= o) wi += y;
     }
-    __syncthreads();
-    return wsum[warp] + inc - x;
+    total = __shfl_sync(kFull, wi, kTileWarps - 1);
+    return __shfl_sync(kFull, wi - w, warp) + inc - x;
 }
 
 // Per-wedge work. MODE 1 sums (count - 1); with 8- and 16-bit counters a thread's or a
@@ -599,10 +604,9 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
         const int64_t ci = cb + tid;
         uint32_t ent = 0;
         if (MODE == 1 && X.single) {
+            // the count pass of this tile found the slices, zeroed the accumulators and
+            // the centre pass's piece counter, and ended with a barrier
             ent = cs.ent[tid];
-            cs.acc[tid] = 0;
-            if (tid == 0) cs.piece_ctr = 0;
-            __syncthreads();
         } else {
             uint32_t start = 0, len = 0;
             if (ci < se) {
@@ -616,8 +620,8 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
             const unsigned long long mine =
                 ((unsigned long long)(islong ? (len + kPiece - 1) / kPiece : 0u) << 32) |
                 ((unsigned long long)(slen != 0u) << 16) | slen;
-            __shared__ unsigned long long s_total;
-            const unsigned long long ex = block_exclusive_scan_u64(mine, &s_total, cs.wsum);
+            unsigned long long total = 0;
+            const unsigned long long ex = block_exclusive_scan_u64(mine, total, cs.wsum);
             cs.start[tid] = start;
             cs.len[tid] = len;
             cs.ent[tid] = ent;
@@ -628,9 +632,11 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
                 cs.sbase[c] = start - off;
                 cs.smeta[c] = (ent & kSignBit) | (uint32_t)tid;
             }
-            if (MODE == 1) cs.acc[tid] = 0;
-            if (tid == 0) cs.piece_ctr = 0;
-            const unsigned long long total = s_total;
+            cs.acc[tid] = 0;
+            if (tid == 0) {
+                cs.piece_ctr = 0;
+                cs.piece_ctr1 = 0;
+            }
             if (tid == kChunk - 1) {
                 const uint32_t nz = (uint32_t)(total >> 16) & 0xffffu;
                 cs.ppiece[kChunk] = (uint32_t)(total >> 32);
@@ -652,26 +658,54 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
             const uint32_t r1 = (uint32_t)(((unsigned long long)NS * (warp + 1)) / kTileWarps);
             if (r0 < r1) {
                 const int nz = (int)cs.nz;
-                int j0 = last_le_n(cs.sP, nz, r0);
-                for (uint32_t r = r0; r < r1; r += 32u) {
-                    // ends of the (up to) 32 slices after j0; each is > r
-                    const int jl = j0 + 1 + lane;
+                // window r: each lane's slice (-1 past r1), the bit mask of the slices that
+                // start inside the window (set bit d: a slice starts at r + d; the ends of
+                // the up to 32 slices after jbase are each > r), and the slice at r + 32
+                auto locate = [&](uint32_t r, int jbase, uint32_t &m, int &j, int &jnext) {
+                    const int jl = jbase + 1 + lane;
                     const uint32_t e = jl <= nz ? cs.sP[jl] : 0xffffffffu;
                     const uint32_t d = e - r;
-                    const uint32_t m = __reduce_or_sync(kFull, d < 32u ? 1u << d : 0u);
+                    m = __reduce_or_sync(kFull, d < 32u ? 1u << d : 0u);
                     const bool at32 = __any_sync(kFull, d == 32u);
-                    const uint32_t k = r + lane;
-                    const int j = k < r1 ? j0 + __popc(m & ((2u << lane) - 1u)) : -1;
-                    uint32_t meta = 0;
+                    j = r + (uint32_t)lane < r1 ? jbase + __popc(m & ((2u << lane) - 1u)) : -1;
+                    jnext = jbase + __popc(m) + (at32 ? 1 : 0);
+                };
+                uint32_t m = 0, x = 0, meta = 0;
+                int j = -1, jn = 0;
+                locate(r0, last_le_n(cs.sP, nz, r0), m, j, jn);
+                if (j >= 0) {
+                    meta = cs.smeta[j];
+                    x = __ldg(rowC + (uint32_t)(cs.sbase[j] + r0 + lane));
+                }
+                for (uint32_t r = r0; r < r1; r += 32u) {
+                    // the next window's entry is loaded before this window's counters are
+                    // touched, so two loads per lane are in flight
+                    uint32_t m2 = 0, x2 = 0, meta2 = 0;
+                    int j2 = -1, jn2 = jn;
+                    if (r + 32u < r1) {
+                        locate(r + 32u, jn, m2, j2, jn2);
+                        if (j2 >= 0) {
+                            meta2 = cs.smeta[j2];
+                            x2 = __ldg(rowC + (uint32_t)(cs.sbase[j2] + r + 32u + lane));
+                        }
+                    }
                     Acc<CW> v = 0;
                     if (j >= 0) {
-                        meta = cs.smeta[j];
-                        wedge<MODE, CW>(ctr, __ldg(rowC + (uint32_t)(cs.sbase[j] + k)),
-                                        Ctr::sign_key(meta & kSignBit), v);
+                        wedge<MODE, CW>(ctr, x, Ctr::sign_key(meta & kSignBit), v);
                         if (MODE == 1) v -= 1u;
                     }
-                    j0 += __popc(m) + (at32 ? 1 : 0);
-                    if (MODE == 1) {
+                    if constexpr (MODE == 1 && CW != 2) {
+                        // lanes of one slice are contiguous and a new slice starts at every
+                        // set bit of m: each lane's group is the run of lanes between two
+                        // such bits, summed by one redux; its first lane adds the sum
+                        const uint32_t upto = (2u << lane) - 1u;
+                        const int g0 = 31 - __clz((m & upto) | 1u);
+                        const uint32_t above = m & ~upto;
+                        const uint32_t hi_mask = above ? (above & (0u - above)) - 1u : kFull;
+                        const uint32_t gmask = hi_mask & ~((1u << g0) - 1u);
+                        const uint32_t tot = __reduce_add_sync(gmask, (uint32_t)v);
+                        if (lane == g0 && j >= 0 && tot) acc_add<CW>(cs, (int)(meta & 0x1ffu), tot);
+                    } else if constexpr (MODE == 1) {
                         // segmented sum over lanes of the same slice (contiguous lanes);
                         // the last lane of each slice adds it
 #pragma unroll
@@ -680,9 +714,14 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
                             const int jj = __shfl_up_sync(kFull, j, o);
                             if (lane >= o && jj == j) v += y;
                         }
-                        const int jn = __shfl_down_sync(kFull, j, 1);
-                        if (j >= 0 && (lane == 31 || jn != j) && v) acc_add<CW>(cs, (int)(meta & 0x1ffu), v);
+                        const int jnb = __shfl_down_sync(kFull, j, 1);
+                        if (j >= 0 && (lane == 31 || jnb != j) && v) acc_add<CW>(cs, (int)(meta & 0x1ffu), v);
                     }
+                    m = m2;
+                    j = j2;
+                    jn = jn2;
+                    x = x2;
+                    meta = meta2;
                 }
             }
         }
@@ -693,7 +732,7 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
             int jw = 0;
             for (;;) {
                 uint32_t pc = 0;
-                if (lane == 0) pc = (uint32_t)atomicAdd(&cs.piece_ctr, 1);
+                if (lane == 0) pc = (uint32_t)atomicAdd(MODE == 0 ? &cs.piece_ctr : &cs.piece_ctr1, 1);
                 pc = __shfl_sync(kFull, pc, 0);
                 if (pc >= NP) break;
                 for (;;) {
@@ -713,7 +752,9 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
                 if ((uint32_t)lane < head) wedge<MODE, CW>(ctr, __ldg(rowC + s + lane), sk, acc);
                 const uint32_t m4 = (n - head) >> 2;
                 const uint4 *v4 = reinterpret_cast<const uint4 *>(rowC + s + head);
-                // two 16-byte loads in flight per lane
+                // two 16-byte loads in flight per lane (and, in the centre pass, two
+                // accumulators so that the additions of the two groups do not chain)
+                Acc<CW> acc2 = 0;
                 for (uint32_t q = lane; q < m4; q += 64) {
                     const uint4 xa = __ldg(v4 + q);
                     const bool has_b = q + 32 < m4;
@@ -723,12 +764,13 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
                     wedge<MODE, CW>(ctr, xa.z, sk, acc);
                     wedge<MODE, CW>(ctr, xa.w, sk, acc);
                     if (has_b) {
-                        wedge<MODE, CW>(ctr, xb.x, sk, acc);
-                        wedge<MODE, CW>(ctr, xb.y, sk, acc);
-                        wedge<MODE, CW>(ctr, xb.z, sk, acc);
-                        wedge<MODE, CW>(ctr, xb.w, sk, acc);
+                        wedge<MODE, CW>(ctr, xb.x, sk, acc2);
+                        wedge<MODE, CW>(ctr, xb.y, sk, acc2);
+                        wedge<MODE, CW>(ctr, xb.z, sk, acc2);
+                        wedge<MODE, CW>(ctr, xb.w, sk, acc2);
                     }
                 }
+                acc += acc2;
                 const uint32_t rest = (n - head) & 3u;
                 if ((uint32_t)lane < rest) wedge<MODE, CW>(ctr, __ldg(rowC + s + head + 4 * m4 + lane), sk, acc);
                 if (MODE == 1) {
