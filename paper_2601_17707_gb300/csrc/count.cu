@@ -454,7 +454,6 @@ struct ChunkSmem {
     unsigned long long acc[kChunk];
     unsigned long long wsum[kTileWarps];
     uint32_t ns, nz;
-    int piece_ctr, piece_ctr1;   // pieces handed out in the count and the centre pass
 };
 // index of the last entry <= k in the non-decreasing p[0..n] (p[0] == 0 <= k)
 __device__ __forceinline__ int last_le_n(const uint32_t *p, int n, uint32_t k) {
@@ -591,8 +590,9 @@ __device__ __forceinline__ unsigned long long acc_get(ChunkSmem &cs, int j) {
 // One pass of the whole block over the oriented wedges of anchor rows [sb, se) whose
 // endpoints lie in [X.lo, X.hi), in chunks of kChunk centres. Per chunk, every thread
 // finds its centre's slice; slices shorter than kLongMin are concatenated and cut into
-// equal contiguous shares, one per thread; longer ones are cut into kPiece-wedge pieces
-// that warps pull from a shared counter and sweep with coalesced 16-byte loads. MODE 0
+// equal contiguous shares, one per warp, read 32 consecutive positions at a time; longer
+// ones are cut into kPiece-wedge pieces that the warps take round robin and sweep with
+// coalesced 16-byte loads. MODE 0
 // bumps the counters; MODE 1 reads them and adds (count - 1) per wedge to the centre's
 // per-vertex sum. A single-chunk MODE 1 pass reuses the slices MODE 0 just found.
 template <int MODE, int CW, class Ctr>
@@ -605,7 +605,7 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
         uint32_t ent = 0;
         if (MODE == 1 && X.single) {
             // the count pass of this tile found the slices, zeroed the accumulators and
-            // the centre pass's piece counter, and ended with a barrier
+            // ended with a barrier
             ent = cs.ent[tid];
         } else {
             uint32_t start = 0, len = 0;
@@ -633,10 +633,6 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
                 cs.smeta[c] = (ent & kSignBit) | (uint32_t)tid;
             }
             cs.acc[tid] = 0;
-            if (tid == 0) {
-                cs.piece_ctr = 0;
-                cs.piece_ctr1 = 0;
-            }
             if (tid == kChunk - 1) {
                 const uint32_t nz = (uint32_t)(total >> 16) & 0xffffu;
                 cs.ppiece[kChunk] = (uint32_t)(total >> 32);
@@ -725,16 +721,13 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
                 }
             }
         }
-        // long slices: pieces pulled by warps. Pieces are handed out in increasing order,
-        // so a warp finds the slice of its next piece by scanning forward from the slice
-        // of its last one, 32 prefix entries per step.
+        // long slices: warp w sweeps pieces w, w + 16, w + 32, ... (pieces are at most
+        // kPiece wedges, so the round robin balances like a shared counter without its
+        // atomics). A warp finds the slice of its next piece by scanning forward from the
+        // slice of its last one, 32 prefix entries per step.
         if (NP) {
             int jw = 0;
-            for (;;) {
-                uint32_t pc = 0;
-                if (lane == 0) pc = (uint32_t)atomicAdd(MODE == 0 ? &cs.piece_ctr : &cs.piece_ctr1, 1);
-                pc = __shfl_sync(kFull, pc, 0);
-                if (pc >= NP) break;
+            for (uint32_t pc = (uint32_t)(tid >> 5); pc < NP; pc += kTileWarps) {
                 for (;;) {
                     const int idx = jw + 1 + lane;
                     const uint32_t val = idx <= kChunk ? cs.ppiece[idx] : 0xffffffffu;
