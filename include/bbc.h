@@ -77,7 +77,10 @@ typedef struct bbc_tuning {
     int32_t plain;             /* 1: the static schedule of G-BBC (Algorithm 3) -- one block
                                   per anchor in rank order, no work queue, no heavy-first
                                   ordering, no hash path, no splitting; for comparisons */
-    int32_t reserved[2];
+    int32_t queue_chunk;       /* work items a warp (or warp group) of the light-anchor
+                                  kernels takes from its queue per atomic access (1..64;
+                                  0: the default, 1) */
+    int32_t reserved;
 } bbc_tuning;
 
 /* Fills *t with the built-in defaults. */
@@ -228,14 +231,25 @@ bbc_status bbc_count_batch(int32_t n, bbc_graph *const *gs, uint64_t *balanced,
                            const bbc_tuning *tuning, void *cuda_stream);
 
 /*
- * bbc_autotune_batch -- times bbc_count_batch over a small grid of tile sizes, hash
- * thresholds and split sizes on these graphs and stores the fastest in *best (and in
- * the library's in-process cache, keyed by the batch's shape, which NULL-tuning batch
- * calls then use). The counts are checked to agree across every candidate;
- * a disagreement returns BBC_E_CUDA.
+ * bbc_autotune_batch -- times bbc_count_batch on these graphs while searching, one knob
+ * at a time from the defaults, the counter-tile size (tile_words), the light-anchor
+ * threshold (warp_max_wedges), the heavy-anchor split size (split_wedges), the resident
+ * blocks per SM and the queue chunk (queue_chunk), and stores the fastest choice in *best.
+ * The choice is also kept for NULL-tuning batch calls on batches of the same shape bucket
+ * (the SM count, the number of graphs and the binary orders of magnitude of their edges,
+ * wedges and pair-side vertices), in the process and in a cache file that later processes
+ * read: $BBC_TUNE_CACHE, else $XDG_CACHE_HOME/bbc/batch_tuning.txt, else
+ * $HOME/.cache/bbc/batch_tuning.txt (an empty BBC_TUNE_CACHE keeps it in the process).
+ * The counts are checked to agree across every candidate; a disagreement returns
+ * BBC_E_CUDA.
  */
 bbc_status bbc_autotune_batch(int32_t n, bbc_graph *const *gs, bbc_tuning *best,
                               void *cuda_stream);
+
+/* The tuning a NULL-tuning bbc_count_batch call would use for these graphs (the cached
+ * choice of bbc_autotune_batch for their shape bucket, else the defaults); split_wedges
+ * is the size chosen for this batch. Host only, no device work. */
+bbc_status bbc_batch_tuning(int32_t n, bbc_graph *const *gs, bbc_tuning *out);
 
 /*
  * Serving loop: requests (edge lists in host memory) are copied, queued, admitted while

@@ -42,6 +42,7 @@ EXPORTS = (
     "bbc_cost_model_loss_grad", "bbc_cost_model_fit", "bbc_cost_model_predict", "bbc_item_features",
     "bbc_item_cycles", "bbc_cost_model_order", "bbc_count_delta", "bbc_graph_work",
     "bbc_item_anchors", "bbc_server_counters_get", "bbc_server_request_info", "bbc_memory_usage",
+    "bbc_batch_tuning",
 )
 
 MOTIF_SIGN_CLASSES = 1
@@ -93,7 +94,8 @@ class Tuning(ctypes.Structure):
         ("split_wedges", ctypes.c_int32),
         ("blocks_per_sm", ctypes.c_int32),
         ("plain", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("queue_chunk", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -126,6 +128,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "bbc_graph_free": ([vp], None),
             "bbc_count_batch": ([i32, vp, vp, ctypes.POINTER(Tuning), vp], ctypes.c_int),
             "bbc_autotune_batch": ([i32, vp, ctypes.POINTER(Tuning), vp], ctypes.c_int),
+            "bbc_batch_tuning": ([i32, vp, ctypes.POINTER(Tuning)], ctypes.c_int),
             "bbc_server_create": ([ctypes.c_size_t, ctypes.POINTER(Tuning), ctypes.POINTER(vp)],
                                   ctypes.c_int),
             "bbc_submit": ([vp, i32, i32, i64, vp, vp, vp, pu64], ctypes.c_int),
@@ -446,6 +449,16 @@ def autotune_batch(graphs: list[Graph], stream=None) -> Tuning:
     hs = (ctypes.c_void_p * max(n, 1))(*[g.handle for g in graphs])
     t = Tuning()
     check(lib.bbc_autotune_batch(n, hs, ctypes.byref(t), _stream_ptr(stream)), "bbc_autotune_batch")
+    return t
+
+
+def batch_tuning(graphs: list[Graph]) -> Tuning:
+    """The tuning a NULL-tuning count_batch call would use for these graphs."""
+    lib = load()
+    n = len(graphs)
+    hs = (ctypes.c_void_p * max(n, 1))(*[g.handle for g in graphs])
+    t = Tuning()
+    check(lib.bbc_batch_tuning(n, hs, ctypes.byref(t)), "bbc_batch_tuning")
     return t
 
 

@@ -190,7 +190,9 @@ Tuning resolve_tuning(const bbc_tuning *t, int sm_count) {
     r.split_wedges = 0;  // 0: chosen per launch from the total work
     r.blocks_per_sm = 2;
     r.plain = 0;
+    r.queue_chunk = 1;
     if (t) {
+        if (t->queue_chunk > 0) r.queue_chunk = t->queue_chunk < 64 ? t->queue_chunk : 64;
         r.plain = t->plain ? 1 : 0;
         if (t->blocks_per_sm == 1 || t->blocks_per_sm == 2) r.blocks_per_sm = t->blocks_per_sm;
         if (t->tile_words > 0) r.tile_words = t->tile_words;
@@ -315,6 +317,7 @@ bbc_status bbc_tuning_default(bbc_tuning *t) {
     t->split_wedges = 0;
     t->blocks_per_sm = r.blocks_per_sm;
     t->plain = 0;
+    t->queue_chunk = r.queue_chunk;
     return BBC_OK;
 }
 

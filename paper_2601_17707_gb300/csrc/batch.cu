@@ -6,10 +6,16 @@
 // launches into a CUDA graph once. Later
 // calls with the same graphs and tuning replay that graph: one launch of the whole
 // counting step, whatever the number of graphs.
+#include <sys/stat.h>
+#include <unistd.h>
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <string>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -75,6 +81,78 @@ constexpr size_t kMaxPlans = 4;
 
 std::mutex g_tune_mu;
 std::map<std::vector<long long>, Tuning> g_tuned;
+bool g_tune_loaded = false;
+
+// The persisted tuning cache: one line per shape key, "key... : tile_words warp_max_wedges
+// split_wedges blocks_per_sm queue_chunk". Its path is $BBC_TUNE_CACHE, else
+// $XDG_CACHE_HOME/bbc/batch_tuning.txt, else $HOME/.cache/bbc/batch_tuning.txt; an empty
+// BBC_TUNE_CACHE turns persistence off.
+std::string tune_cache_path() {
+    if (const char *p = getenv("BBC_TUNE_CACHE")) return std::string(p);
+    if (const char *x = getenv("XDG_CACHE_HOME"); x && *x) return std::string(x) + "/bbc/batch_tuning.txt";
+    if (const char *h = getenv("HOME"); h && *h) return std::string(h) + "/.cache/bbc/batch_tuning.txt";
+    return std::string();
+}
+
+void load_tune_cache_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const std::string path = tune_cache_path();
+    if (path.empty()) return;
+    FILE *f = fopen(path.c_str(), "r");
+    if (!f) return;
+    char line[512];
+    while (fgets(line, sizeof line, f)) {
+        std::vector<long long> key;
+        char *colon = strchr(line, ':');
+        if (!colon) continue;
+        *colon = 0;
+        char *p = line, *end = nullptr;
+        for (;;) {
+            const long long v = strtoll(p, &end, 10);
+            if (end == p) break;
+            key.push_back(v);
+            p = end;
+        }
+        long long tw = 0, wm = 0, sp = 0, bp = 0, qc = 0;
+        if (key.size() != 5 ||
+            sscanf(colon + 1, "%lld %lld %lld %lld %lld", &tw, &wm, &sp, &bp, &qc) != 5)
+            continue;
+        bbc_tuning t{};
+        t.tile_words = (int32_t)tw;
+        t.warp_max_wedges = (int32_t)wm;
+        t.split_wedges = (int32_t)std::min<long long>(sp, INT32_MAX);
+        t.blocks_per_sm = (int32_t)bp;
+        t.queue_chunk = (int32_t)qc;
+        g_tuned[key] = resolve_tuning(&t, device_sm_count());
+    }
+    fclose(f);
+}
+
+// Rewrites the cache file with every tuned entry of this process (best effort: a cache
+// that cannot be written only costs a new search next time).
+void save_tune_cache_locked() {
+    const std::string path = tune_cache_path();
+    if (path.empty()) return;
+    const size_t slash = path.rfind('/');
+    if (slash != std::string::npos) {
+        // create the directory chain (mkdir -p)
+        for (size_t i = 1; i <= slash; ++i)
+            if (path[i] == '/' || i == slash) mkdir(path.substr(0, i == slash ? slash : i).c_str(), 0755);
+    }
+    const std::string tmp = path + ".tmp" + std::to_string((long long)getpid());
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    for (const auto &kv : g_tuned) {
+        for (long long v : kv.first) fprintf(f, "%lld ", v);
+        const Tuning &t = kv.second;
+        fprintf(f, ": %d %d %lld %d %d\n", t.tile_words, t.warp_max_wedges, t.split_wedges,
+                t.blocks_per_sm, t.queue_chunk);
+    }
+    const bool ok = fclose(f) == 0;
+    if (ok) rename(tmp.c_str(), path.c_str());
+    else remove(tmp.c_str());
+}
 
 std::vector<long long> shape_key(int32_t n, bbc_graph *const *gs) {
     long long e = 0, w = 0, s = 0;
@@ -92,13 +170,13 @@ std::vector<long long> shape_key(int32_t n, bbc_graph *const *gs) {
         }
         return (long long)b;
     };
-    return {n, bucket(e), bucket(w), bucket(s)};
+    return {device_sm_count(), n, bucket(e), bucket(w), bucket(s)};
 }
 
 bool same_tuning(const Tuning &a, const Tuning &b) {
     return a.tile_words == b.tile_words && a.warp_max_wedges == b.warp_max_wedges &&
            a.split_wedges == b.split_wedges && a.blocks_per_sm == b.blocks_per_sm &&
-           a.plain == b.plain;
+           a.plain == b.plain && a.queue_chunk == b.queue_chunk;
 }
 
 #define BBC_LAUNCH_OK(what)                                        \
@@ -325,6 +403,7 @@ Tuning batch_tuning(int32_t n, bbc_graph *const *gs, const bbc_tuning *t) {
     Tuning T = resolve_tuning(t, device_sm_count());
     if (!t) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
+        load_tune_cache_locked();
         auto it = g_tuned.find(shape_key(n, gs));
         if (it != g_tuned.end()) T = it->second;
     }
@@ -394,23 +473,11 @@ bbc_status bbc_autotune_batch(int32_t n, bbc_graph *const *gs, bbc_tuning *best,
     try {
         BBC_TRY(check_graphs(n, gs));
         cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-        struct Cand {
-            int tile_words, blocks_per_sm, warp_max;
-        };
-        // tile_words 0 = the largest tile for the residency
-        const Cand cands[] = {
-            {0, 2, 256}, {0, 2, 64}, {0, 2, 512}, {16384, 2, 256},
-            {8192, 2, 256}, {0, 1, 256}, {8192, 2, 512}, {4096, 2, 512},
-        };
+        // coordinate search from the defaults: each knob in turn over its candidates,
+        // keeping the fastest value before moving to the next knob
         std::vector<uint64_t> ref(std::max(n, 1)), got(std::max(n, 1));
         bool have_ref = false;
-        float best_ms = 1e30f;
-        bbc_tuning best_t{};
-        for (const Cand &c : cands) {
-            bbc_tuning t{};
-            t.tile_words = c.tile_words;
-            t.blocks_per_sm = c.blocks_per_sm;
-            t.warp_max_wedges = c.warp_max;
+        auto timed = [&](const bbc_tuning &t, float *out_ms) -> bbc_status {
             float ms_best = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
                 float ms = 0.f;
@@ -424,19 +491,75 @@ bbc_status bbc_autotune_batch(int32_t n, bbc_graph *const *gs, bbc_tuning *best,
                 set_error("bbc_autotune_batch: candidates disagree on the counts");
                 return BBC_E_CUDA;
             }
-            if (ms_best < best_ms) {
-                best_ms = ms_best;
-                best_t = t;
+            *out_ms = ms_best;
+            return BBC_OK;
+        };
+        uint64_t wsum = 0;
+        for (int i = 0; i < n; ++i) wsum += gs[i]->wedges;
+        const long long s_auto = auto_split(wsum, device_sm_count(), 2);
+        bbc_tuning best_t{};
+        best_t.blocks_per_sm = 2;
+        best_t.warp_max_wedges = 256;
+        best_t.queue_chunk = 1;
+        float best_ms = 1e30f;
+        BBC_TRY(timed(best_t, &best_ms));
+        const std::vector<int> knob_tiles = {0, 16384, 8192, 4096};
+        const std::vector<int> knob_warp = {64, 256, 512};
+        const std::vector<int> knob_blocks = {1, 2};
+        const std::vector<int> knob_chunk = {1, 4, 16};
+        const std::vector<long long> knob_split = {s_auto / 4, s_auto, 4 * s_auto};
+        auto sweep = [&](auto values, auto set) -> bbc_status {
+            bbc_tuning keep = best_t;
+            for (auto v : values) {
+                bbc_tuning t = keep;
+                set(t, v);
+                if (memcmp(&t, &keep, sizeof t) == 0) continue;
+                float ms = 0.f;
+                BBC_TRY(timed(t, &ms));
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_t = t;
+                }
             }
-        }
+            return BBC_OK;
+        };
+        BBC_TRY(sweep(knob_tiles, [](bbc_tuning &t, int v) { t.tile_words = v; }));
+        BBC_TRY(sweep(knob_warp, [](bbc_tuning &t, int v) { t.warp_max_wedges = v; }));
+        BBC_TRY(sweep(knob_split, [](bbc_tuning &t, long long v) {
+            t.split_wedges = (int32_t)std::min<long long>(std::max<long long>(v, 1), INT32_MAX);
+        }));
+        BBC_TRY(sweep(knob_blocks, [](bbc_tuning &t, int v) { t.blocks_per_sm = v; }));
+        BBC_TRY(sweep(knob_chunk, [](bbc_tuning &t, int v) { t.queue_chunk = v; }));
         *best = best_t;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
+            load_tune_cache_locked();
             g_tuned[shape_key(n, gs)] = resolve_tuning(&best_t, device_sm_count());
+            save_tune_cache_locked();
         }
         return BBC_OK;
     } catch (...) {
         set_error("unexpected exception in bbc_autotune_batch");
+        return BBC_E_CUDA;
+    }
+}
+
+bbc_status bbc_batch_tuning(int32_t n, bbc_graph *const *gs, bbc_tuning *out) {
+    if (!out) return BBC_E_INVALID_ARG;
+    try {
+        BBC_TRY(check_graphs(n, gs));
+        const Tuning T = batch_tuning(n, gs, nullptr);
+        memset(out, 0, sizeof *out);
+        out->tile_words = T.tile_words;
+        out->warp_max_wedges = T.warp_max_wedges;
+        out->dense_min_permille = T.dense_min_permille;
+        out->split_wedges = (int32_t)std::min<long long>(T.split_wedges, INT32_MAX);
+        out->blocks_per_sm = T.blocks_per_sm;
+        out->plain = T.plain;
+        out->queue_chunk = T.queue_chunk;
+        return BBC_OK;
+    } catch (...) {
+        set_error("unexpected exception in bbc_batch_tuning");
         return BBC_E_CUDA;
     }
 }

@@ -137,6 +137,7 @@ struct Tuning {
     int blocks_per_sm;
     int plain;                 // static one-block-per-anchor schedule (Algorithm 3)
     int tiles_only = 0;        // every anchor on block tiles (no hash or warp/group tiles)
+    int queue_chunk = 1;       // items per queue access of the warp and group kernels
 };
 
 Tuning resolve_tuning(const bbc_tuning *t, int sm_count);

@@ -114,6 +114,11 @@ struct HashCounter {
         }
         atomicOr(err, kErrHashFull);
     }
+    __device__ static __forceinline__ uint32_t sign_key(uint32_t sg) { return sg; }
+    __device__ __forceinline__ void bump_entry(uint32_t x, uint32_t sg) const { bump(x & kIdMask, (x ^ sg) >> 31); }
+    __device__ __forceinline__ uint32_t count_entry(uint32_t x, uint32_t sg) const {
+        return peek(x & kIdMask, (x ^ sg) >> 31);
+    }
     __device__ __forceinline__ uint32_t peek(uint32_t w, uint32_t t) const {
         uint32_t h = home(w);
         for (uint32_t probe = 0; probe <= mask; ++probe) {
@@ -128,152 +133,6 @@ struct HashCounter {
 };
 
 // ----------------------------------------------------------------------------- sweep
-
-// Per-warp staging of one batch of 32 centres' short slices (the warp sweep's table).
-struct WarpStage {
-    uint32_t start[32];
-    uint32_t excl[33];
-    uint32_t sg[32];
-};
-
-// One warp's pass over all oriented wedges of anchor rows [sb, se) (the warp kernels'
-// sweep: their anchors fit one counter table). MODE 0 bumps the counters; MODE 1 (the
-// per-vertex centre pass) reads them and adds (count - 1) per wedge to the centre's b.
-// Warps take batches of 32 centres from *batch_ctr; lane j owns centre j's slice. Long
-// slices are swept by the whole warp with 16-byte loads; short ones are concatenated in
-// the warp's stage and cut into contiguous per-lane shares.
-template <int MODE, class Counter>
-__device__ __forceinline__ void warp_sweep(const DevGraph &G, int64_t sb, int64_t se,
-                                      const Counter &ctr, int *batch_ctr, uint32_t *sacc,
-                                      WarpStage &ws) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nbatch = (se - sb + 31) >> 5;
-    const uint32_t *__restrict__ rowC = G.rowC;
-    for (;;) {
-        int bi = 0;
-        if (lane == 0) bi = atomicAdd(batch_ctr, 1);
-        bi = __shfl_sync(kFull, bi, 0);
-        if (bi >= nbatch) break;
-        const int64_t ci = sb + (int64_t)bi * 32 + lane;
-        uint32_t b = 0, len = 0, sg = 0, c = 0;
-        if (ci < se) {
-            // the whole endpoint range of the anchor inside row c (known from preparation)
-            const uint32_t ent = __ldg(G.rowS + ci);
-            c = ent & kIdMask;
-            sg = ent & kSignBit;
-            const uint2 r = __ldg(G.rng + ci);
-            b = r.x;
-            len = r.y - r.x;
-        }
-        // Long slices: the whole warp sweeps one slice at a time, coalesced 16-byte loads.
-        unsigned longm = __ballot_sync(kFull, len >= (uint32_t)kLongSlice);
-        while (longm) {
-            const int j = __ffs(longm) - 1;
-            longm &= longm - 1;
-            const uint32_t s = __shfl_sync(kFull, b, j);
-            const uint32_t n = __shfl_sync(kFull, len, j);
-            const uint32_t sj = __shfl_sync(kFull, sg, j);
-            unsigned long long acc = 0;
-            auto visit = [&](uint32_t x) {
-                if (MODE == 0)
-                    ctr.bump(x & kIdMask, (x ^ sj) >> 31);
-                else
-                    acc += ctr.peek(x & kIdMask, (x ^ sj) >> 31) - 1u;
-            };
-            const uint32_t head = min(n, (4u - (s & 3u)) & 3u);
-            if ((uint32_t)lane < head) visit(__ldg(rowC + s + lane));
-            const uint32_t m4 = (n - head) >> 2;
-            const uint4 *v4 = reinterpret_cast<const uint4 *>(rowC + s + head);
-            for (uint32_t q = lane; q < m4; q += 64) {
-                const uint4 xa = __ldg(v4 + q);
-                const bool has_b = q + 32 < m4;
-                uint4 xb = make_uint4(0u, 0u, 0u, 0u);
-                if (has_b) xb = __ldg(v4 + q + 32);
-                visit(xa.x);
-                visit(xa.y);
-                visit(xa.z);
-                visit(xa.w);
-                if (has_b) {
-                    visit(xb.x);
-                    visit(xb.y);
-                    visit(xb.z);
-                    visit(xb.w);
-                }
-            }
-            const uint32_t rest = (n - head) & 3u;
-            if ((uint32_t)lane < rest) visit(__ldg(rowC + s + head + 4 * m4 + lane));
-            if (MODE == 1) {
-                acc = warp_sum(acc);
-                if (lane == j && acc) red_add(G.bC + c, acc);
-            }
-        }
-        // Short slices: staged, then contiguous equal shares per lane.
-        const uint32_t sl = len < (uint32_t)kLongSlice ? len : 0u;
-        uint32_t incl = sl;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const uint32_t total = __shfl_sync(kFull, incl, 31);
-        ws.start[lane] = b;
-        ws.excl[lane] = incl - sl;
-        ws.sg[lane] = sg;
-        if (lane == 31) ws.excl[32] = total;
-        if (MODE == 1) sacc[lane] = 0;
-        __syncwarp();
-        uint32_t k = (uint32_t)(((unsigned long long)total * lane) >> 5);
-        const uint32_t k1 = (uint32_t)(((unsigned long long)total * (lane + 1)) >> 5);
-        if (k < k1) {
-            int j = 0;  // last staged slice whose start offset is <= k
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1)
-                if (ws.excl[j + step] <= k) j += step;
-            uint32_t nb = ws.excl[j + 1];
-            uint32_t base = ws.start[j] - ws.excl[j];
-            uint32_t sgj = ws.sg[j];
-            uint32_t acc = 0;
-            uint32_t x = __ldg(rowC + (uint32_t)(base + k));
-            for (;;) {
-                const uint32_t k2 = k + 1;
-                int j2 = j;
-                uint32_t nb2 = nb, base2 = base, sg2 = sgj, x2 = 0;
-                if (k2 < k1) {
-                    if (k2 >= nb2) {
-                        do {
-                            ++j2;
-                            nb2 = ws.excl[j2 + 1];
-                        } while (nb2 <= k2);
-                        base2 = ws.start[j2] - ws.excl[j2];
-                        sg2 = ws.sg[j2];
-                    }
-                    x2 = __ldg(rowC + (uint32_t)(base2 + k2));
-                }
-                if (MODE == 0)
-                    ctr.bump(x & kIdMask, (x ^ sgj) >> 31);
-                else
-                    acc += ctr.peek(x & kIdMask, (x ^ sgj) >> 31) - 1u;
-                if (k2 >= k1) break;
-                if (MODE == 1 && j2 != j && acc) {
-                    atomicAdd(sacc + j, acc);
-                    acc = 0;
-                }
-                k = k2;
-                j = j2;
-                nb = nb2;
-                base = base2;
-                sgj = sg2;
-                x = x2;
-            }
-            if (MODE == 1 && acc) atomicAdd(sacc + j, acc);
-        }
-        __syncwarp();
-        if (MODE == 1) {
-            if (sl > 0 && sacc[lane]) red_add(G.bC + c, sacc[lane]);
-            __syncwarp();
-        }
-    }
-}
 
 // ----------------------------------------------------------------------------- tiles
 
@@ -521,6 +380,207 @@ __device__ __forceinline__ void wedge(const Ctr &ctr, uint32_t x, uint32_t sk, A
 __device__ __forceinline__ uint32_t warp_total(uint32_t x) { return __reduce_add_sync(kFull, x); }
 __device__ __forceinline__ unsigned long long warp_total(unsigned long long x) { return warp_sum(x); }
 
+// One wedge for any counter and accumulator type (wedge() without the width).
+template <int MODE, class Ctr, class A>
+__device__ __forceinline__ void wedge_any(const Ctr &ctr, uint32_t x, uint32_t sk, A &acc) {
+    if constexpr (MODE == 0)
+        ctr.bump_entry(x, sk);
+    else
+        acc += ctr.count_entry(x, sk);
+}
+
+// Lane-interleaved walk over positions [r0, r1) of a run of concatenated short slices, 32
+// consecutive positions per step with lane L on position r + L, so that lanes on one
+// slice read consecutive entries (coalesced). sP[0..nz] are the slices' starts in the
+// concatenation (strictly increasing; sP[nz] is the total), sbase[j] is the rowC index of
+// slice j's first entry minus sP[j], and smeta[j] holds the anchor edge's sign bit and a
+// tag below 2^31. A lane's slice is the window's first slice plus the number of slice
+// starts at or before its position, counted from a bit mask of the starts inside the
+// window. The next window's entry is loaded before this window's counters are touched,
+// so two loads per lane are in flight. MODE 1 hands each run of lanes on one slice, once
+// per window, to add(tag, sum over its wedges of count - 1).
+template <int MODE, class A, class Ctr, class Add>
+__device__ __forceinline__ void walk_short(const Ctr &ctr, const uint32_t *__restrict__ rowC,
+                                           const uint32_t *sP, const uint32_t *sbase,
+                                           const uint32_t *smeta, int nz, uint32_t r0, uint32_t r1,
+                                           Add &&add) {
+    const int lane = threadIdx.x & 31;
+    // window r: each lane's slice (-1 past r1), the bit mask of the slices that start
+    // inside the window (set bit d: a slice starts at r + d; the starts of the up to 32
+    // slices after jbase all lie past r), and the slice at position r + 32
+    auto locate = [&](uint32_t r, int jbase, uint32_t &m, int &j, int &jnext) {
+        const int jl = jbase + 1 + lane;
+        const uint32_t e = jl <= nz ? sP[jl] : 0xffffffffu;
+        const uint32_t d = e - r;
+        m = __reduce_or_sync(kFull, d < 32u ? 1u << d : 0u);
+        const bool at32 = __any_sync(kFull, d == 32u);
+        j = r + (uint32_t)lane < r1 ? jbase + __popc(m & ((2u << lane) - 1u)) : -1;
+        jnext = jbase + __popc(m) + (at32 ? 1 : 0);
+    };
+    uint32_t m = 0, x = 0, meta = 0;
+    int j = -1, jn = 0;
+    locate(r0, last_le_n(sP, nz, r0), m, j, jn);
+    if (j >= 0) {
+        meta = smeta[j];
+        x = __ldg(rowC + (uint32_t)(sbase[j] + r0 + lane));
+    }
+    for (uint32_t r = r0; r < r1; r += 32u) {
+        uint32_t m2 = 0, x2 = 0, meta2 = 0;
+        int j2 = -1, jn2 = jn;
+        if (r + 32u < r1) {
+            locate(r + 32u, jn, m2, j2, jn2);
+            if (j2 >= 0) {
+                meta2 = smeta[j2];
+                x2 = __ldg(rowC + (uint32_t)(sbase[j2] + r + 32u + lane));
+            }
+        }
+        A v = 0;
+        if (j >= 0) {
+            wedge_any<MODE>(ctr, x, Ctr::sign_key(meta & kSignBit), v);
+            if (MODE == 1) v -= 1u;
+        }
+        if constexpr (MODE == 1 && sizeof(A) == 4) {
+            // lanes of one slice are contiguous and a new slice starts at every set bit of
+            // m: each lane's group is the run of lanes between two such bits, summed by
+            // one redux; its first lane hands the sum on
+            const uint32_t upto = (2u << lane) - 1u;
+            const int g0 = 31 - __clz((m & upto) | 1u);
+            const uint32_t above = m & ~upto;
+            const uint32_t hi_mask = above ? (above & (0u - above)) - 1u : kFull;
+            const uint32_t gmask = hi_mask & ~((1u << g0) - 1u);
+            const uint32_t tot = __reduce_add_sync(gmask, (uint32_t)v);
+            if (lane == g0 && j >= 0 && tot) add(meta & kIdMask, (A)tot);
+        } else if constexpr (MODE == 1) {
+            // segmented sum over lanes of the same slice; the last lane of each hands it on
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const A y = __shfl_up_sync(kFull, v, o);
+                const int jj = __shfl_up_sync(kFull, j, o);
+                if (lane >= o && jj == j) v += y;
+            }
+            const int jnb = __shfl_down_sync(kFull, j, 1);
+            if (j >= 0 && (lane == 31 || jnb != j) && v) add(meta & kIdMask, v);
+        }
+        m = m2;
+        j = j2;
+        jn = jn2;
+        x = x2;
+        meta = meta2;
+    }
+}
+
+// Per-warp staging of one batch of 32 centres' short slices (the warp sweep's table):
+// the compacted non-empty short slices in lane order, as walk_short reads them.
+struct WarpStage {
+    uint32_t sP[33];
+    uint32_t sbase[32];
+    uint32_t meta[32];
+};
+
+// One warp's pass over all oriented wedges of anchor rows [sb, se) (the warp kernels'
+// sweep: their anchors fit one counter table). MODE 0 bumps the counters; MODE 1 (the
+// per-vertex centre pass) reads them and adds (count - 1) per wedge to the centre's b.
+// Warps take batches of 32 centres from *batch_ctr; lane j owns centre j's slice. Long
+// slices are swept by the whole warp with 16-byte loads; short ones are compacted into
+// the warp's stage and walked lane-interleaved (walk_short). Per-centre sums of a batch
+// stay below 2^32: a slice's counts add up to at most the number of edges.
+template <int MODE, class Counter>
+__device__ __forceinline__ void warp_sweep(const DevGraph &G, int64_t sb, int64_t se,
+                                      const Counter &ctr, int *batch_ctr, uint32_t *sacc,
+                                      WarpStage &ws) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nbatch = (se - sb + 31) >> 5;
+    const uint32_t *__restrict__ rowC = G.rowC;
+    for (;;) {
+        int bi = 0;
+        if (lane == 0) bi = atomicAdd(batch_ctr, 1);
+        bi = __shfl_sync(kFull, bi, 0);
+        if (bi >= nbatch) break;
+        const int64_t ci = sb + (int64_t)bi * 32 + lane;
+        uint32_t b = 0, len = 0, sg = 0, c = 0;
+        if (ci < se) {
+            // the whole endpoint range of the anchor inside row c (known from preparation)
+            const uint32_t ent = __ldg(G.rowS + ci);
+            c = ent & kIdMask;
+            sg = ent & kSignBit;
+            const uint2 r = __ldg(G.rng + ci);
+            b = r.x;
+            len = r.y - r.x;
+        }
+        // Long slices: the whole warp sweeps one slice at a time, coalesced 16-byte loads.
+        unsigned longm = __ballot_sync(kFull, len >= (uint32_t)kLongSlice);
+        while (longm) {
+            const int j = __ffs(longm) - 1;
+            longm &= longm - 1;
+            const uint32_t s = __shfl_sync(kFull, b, j);
+            const uint32_t n = __shfl_sync(kFull, len, j);
+            const uint32_t sj = Counter::sign_key(__shfl_sync(kFull, sg, j));
+            uint32_t acc = 0;
+            auto visit = [&](uint32_t x) {
+                if (MODE == 0)
+                    ctr.bump_entry(x, sj);
+                else
+                    acc += ctr.count_entry(x, sj);
+            };
+            const uint32_t head = min(n, (4u - (s & 3u)) & 3u);
+            if ((uint32_t)lane < head) visit(__ldg(rowC + s + lane));
+            const uint32_t m4 = (n - head) >> 2;
+            const uint4 *v4 = reinterpret_cast<const uint4 *>(rowC + s + head);
+            for (uint32_t q = lane; q < m4; q += 64) {
+                const uint4 xa = __ldg(v4 + q);
+                const bool has_b = q + 32 < m4;
+                uint4 xb = make_uint4(0u, 0u, 0u, 0u);
+                if (has_b) xb = __ldg(v4 + q + 32);
+                visit(xa.x);
+                visit(xa.y);
+                visit(xa.z);
+                visit(xa.w);
+                if (has_b) {
+                    visit(xb.x);
+                    visit(xb.y);
+                    visit(xb.z);
+                    visit(xb.w);
+                }
+            }
+            const uint32_t rest = (n - head) & 3u;
+            if ((uint32_t)lane < rest) visit(__ldg(rowC + s + head + 4 * m4 + lane));
+            if (MODE == 1) {
+                const uint32_t tot = warp_total(acc) - n;
+                if (lane == j && tot) red_add(G.bC + c, tot);
+            }
+        }
+        // Short slices: compacted in lane order, then walked lane-interleaved.
+        const bool isshort = len > 0 && len < (uint32_t)kLongSlice;
+        const unsigned smask = __ballot_sync(kFull, isshort);
+        const uint32_t sl = isshort ? len : 0u;
+        uint32_t incl = sl;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        const int nzs = __popc(smask);
+        if (isshort) {
+            const int cj = __popc(smask & ((1u << lane) - 1u));
+            ws.sP[cj] = incl - sl;
+            ws.sbase[cj] = b - (incl - sl);
+            ws.meta[cj] = sg | (uint32_t)lane;
+        }
+        if (lane == 0) ws.sP[nzs] = total;
+        if (MODE == 1) sacc[lane] = 0;
+        __syncwarp();
+        if (total)
+            walk_short<MODE, uint32_t>(ctr, rowC, ws.sP, ws.sbase, ws.meta, nzs, 0u, total,
+                                       [&](uint32_t tag, uint32_t v) { atomicAdd(sacc + tag, v); });
+        __syncwarp();
+        if (MODE == 1) {
+            if (isshort && sacc[lane]) red_add(G.bC + c, sacc[lane]);
+            __syncwarp();
+        }
+    }
+}
+
 // First index of row[b, lim) whose rank is >= key (the row is sorted by rank), found by
 // galloping from b: about 2 log2 of the distance instead of log2 of the row length.
 __device__ __forceinline__ uint32_t gallop_rank(const uint32_t *__restrict__ row, uint32_t b,
@@ -652,74 +712,9 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
             const int warp = tid >> 5;
             const uint32_t r0 = (uint32_t)(((unsigned long long)NS * warp) / kTileWarps);
             const uint32_t r1 = (uint32_t)(((unsigned long long)NS * (warp + 1)) / kTileWarps);
-            if (r0 < r1) {
-                const int nz = (int)cs.nz;
-                // window r: each lane's slice (-1 past r1), the bit mask of the slices that
-                // start inside the window (set bit d: a slice starts at r + d; the ends of
-                // the up to 32 slices after jbase are each > r), and the slice at r + 32
-                auto locate = [&](uint32_t r, int jbase, uint32_t &m, int &j, int &jnext) {
-                    const int jl = jbase + 1 + lane;
-                    const uint32_t e = jl <= nz ? cs.sP[jl] : 0xffffffffu;
-                    const uint32_t d = e - r;
-                    m = __reduce_or_sync(kFull, d < 32u ? 1u << d : 0u);
-                    const bool at32 = __any_sync(kFull, d == 32u);
-                    j = r + (uint32_t)lane < r1 ? jbase + __popc(m & ((2u << lane) - 1u)) : -1;
-                    jnext = jbase + __popc(m) + (at32 ? 1 : 0);
-                };
-                uint32_t m = 0, x = 0, meta = 0;
-                int j = -1, jn = 0;
-                locate(r0, last_le_n(cs.sP, nz, r0), m, j, jn);
-                if (j >= 0) {
-                    meta = cs.smeta[j];
-                    x = __ldg(rowC + (uint32_t)(cs.sbase[j] + r0 + lane));
-                }
-                for (uint32_t r = r0; r < r1; r += 32u) {
-                    // the next window's entry is loaded before this window's counters are
-                    // touched, so two loads per lane are in flight
-                    uint32_t m2 = 0, x2 = 0, meta2 = 0;
-                    int j2 = -1, jn2 = jn;
-                    if (r + 32u < r1) {
-                        locate(r + 32u, jn, m2, j2, jn2);
-                        if (j2 >= 0) {
-                            meta2 = cs.smeta[j2];
-                            x2 = __ldg(rowC + (uint32_t)(cs.sbase[j2] + r + 32u + lane));
-                        }
-                    }
-                    Acc<CW> v = 0;
-                    if (j >= 0) {
-                        wedge<MODE, CW>(ctr, x, Ctr::sign_key(meta & kSignBit), v);
-                        if (MODE == 1) v -= 1u;
-                    }
-                    if constexpr (MODE == 1 && CW != 2) {
-                        // lanes of one slice are contiguous and a new slice starts at every
-                        // set bit of m: each lane's group is the run of lanes between two
-                        // such bits, summed by one redux; its first lane adds the sum
-                        const uint32_t upto = (2u << lane) - 1u;
-                        const int g0 = 31 - __clz((m & upto) | 1u);
-                        const uint32_t above = m & ~upto;
-                        const uint32_t hi_mask = above ? (above & (0u - above)) - 1u : kFull;
-                        const uint32_t gmask = hi_mask & ~((1u << g0) - 1u);
-                        const uint32_t tot = __reduce_add_sync(gmask, (uint32_t)v);
-                        if (lane == g0 && j >= 0 && tot) acc_add<CW>(cs, (int)(meta & 0x1ffu), tot);
-                    } else if constexpr (MODE == 1) {
-                        // segmented sum over lanes of the same slice (contiguous lanes);
-                        // the last lane of each slice adds it
-#pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const Acc<CW> y = __shfl_up_sync(kFull, v, o);
-                            const int jj = __shfl_up_sync(kFull, j, o);
-                            if (lane >= o && jj == j) v += y;
-                        }
-                        const int jnb = __shfl_down_sync(kFull, j, 1);
-                        if (j >= 0 && (lane == 31 || jnb != j) && v) acc_add<CW>(cs, (int)(meta & 0x1ffu), v);
-                    }
-                    m = m2;
-                    j = j2;
-                    jn = jn2;
-                    x = x2;
-                    meta = meta2;
-                }
-            }
+            if (r0 < r1)
+                walk_short<MODE, Acc<CW>>(ctr, rowC, cs.sP, cs.sbase, cs.smeta, (int)cs.nz, r0, r1,
+                                          [&](uint32_t tag, Acc<CW> v) { acc_add<CW>(cs, (int)tag, v); });
         }
         // long slices: warp w sweeps pieces w, w + 16, w + 32, ... (pieces are at most
         // kPiece wedges, so the round robin balances like a shared counter without its
@@ -985,7 +980,7 @@ k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, 
 
 __global__ void __launch_bounds__(kHashThreads)
 k_warp_hash(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ items, int n_items,
-            QueueState *q) {
+            QueueState *q, int chunk) {
     extern __shared__ uint4 smem_hash[];
     __shared__ uint32_t s_acc[kHashWarps][32];
     __shared__ int s_batch[kHashWarps];
@@ -998,10 +993,15 @@ k_warp_hash(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ it
         vals[i] = 0;
     }
     __syncwarp();
-    for (;;) {
-        int it = 0;
-        if (lane == 0) it = (int)atomicAdd(&q->warp_head, 1u);
-        it = __shfl_sync(kFull, it, 0);
+    // items come `chunk` at a time from the queue, so that the head's atomics do not
+    // serialise a stream of light anchors
+    int it = 0, it_end = 0;
+    for (;; ++it) {
+        if (it >= it_end) {
+            if (lane == 0) it = (int)atomicAdd(&q->warp_head, (unsigned)chunk);
+            it = __shfl_sync(kFull, it, 0);
+            it_end = min(it + chunk, n_items);
+        }
         if (it >= n_items) break;
         const HashItem item = items[it];
         const DevGraph &G = graphs[item.graph];
@@ -1106,9 +1106,10 @@ __device__ void group_tile_item(const DevGraph &G, int a, uint32_t *tile, int gr
     const int lane = threadIdx.x & 31;
     const int gt = threadIdx.x - grp * GW * 32;
     const int64_t sb = G.rowS_off[a], se = G.rowS_off[a + 1];
-    const uint32_t lo = G.orient_low ? 0u : (uint32_t)a + 1u;
+    const uint32_t lo0 = G.orient_low ? 0u : (uint32_t)a + 1u;
     const uint32_t hi = G.orient_low ? (uint32_t)a : (uint32_t)G.nS;
-    const TileCounter<CW> ctr{tile, lo};
+    const BlockTile<CW> ctr(tile, lo0);
+    const uint32_t lo = BlockTile<CW>::origin(lo0);   // the table's first endpoint slot
     if (gt == 0) *batch_ctr = 0;
     group_sync<GW>(grp);
     warp_sweep<0>(G, sb, se, ctr, batch_ctr, nullptr, ws);
@@ -1158,7 +1159,7 @@ __device__ void group_tile_item(const DevGraph &G, int a, uint32_t *tile, int gr
 template <int GW>
 __global__ void __launch_bounds__(kWtThreads, 2)
 k_group_tile(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ items, int n_items,
-             unsigned *head) {
+             unsigned *head, int chunk) {
     extern __shared__ uint4 smem_wt[];
     __shared__ uint32_t s_acc[kWtWarps][32];
     __shared__ int s_batch[kWtWarps / GW];
@@ -1169,10 +1170,16 @@ k_group_tile(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ i
     const int gt = threadIdx.x - grp * GW * 32;
     uint32_t *tile = reinterpret_cast<uint32_t *>(smem_wt) + grp * (GW * kWtWords);
     for (int i = gt; i < GW * kWtWords; i += GW * 32) tile[i] = 0;
-    for (;;) {
-        if (gt == 0) s_item[grp] = (int)atomicAdd(head, 1u);
-        group_sync<GW>(grp);
-        const int it = s_item[grp];
+    // items come `chunk` at a time from the queue (see k_warp_hash)
+    int it = 0, it_end = 0;
+    for (;; ++it) {
+        if (it >= it_end) {
+            if (gt == 0) s_item[grp] = (int)atomicAdd(head, (unsigned)chunk);
+            group_sync<GW>(grp);
+            it = s_item[grp];
+            it_end = min(it + chunk, n_items);
+            group_sync<GW>(grp);
+        }
         if (it >= n_items) break;
         const HashItem item = items[it];
         const DevGraph &G = graphs[item.graph];
@@ -1462,7 +1469,7 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
         constexpr int groups = kWtWarps / kGroupWarps;
         k_group_tile<kGroupWarps><<<std::min((L.n_gt_items + groups - 1) / groups, sms * 2), kWtThreads,
                                     kWtWarps * kWtWords * 4, st>>>(
-            L.graphs, L.gt_items, L.n_gt_items, &L.queue->gt_head);
+            L.graphs, L.gt_items, L.n_gt_items, &L.queue->gt_head, T.queue_chunk);
         BBC_CUDA_TRY(cudaGetLastError());
         profile_end(tok, st);
         BBC_TRY(end_side(st));
@@ -1473,7 +1480,7 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
         note_launch();
         k_group_tile<1><<<std::min((L.n_wt_items + kWtWarps - 1) / kWtWarps, sms * 2), kWtThreads,
                           kWtWarps * kWtWords * 4, st>>>(
-            L.graphs, L.wt_items, L.n_wt_items, &L.queue->wt_head);
+            L.graphs, L.wt_items, L.n_wt_items, &L.queue->wt_head, T.queue_chunk);
         BBC_CUDA_TRY(cudaGetLastError());
         profile_end(tok, st);
         BBC_TRY(end_side(st));
@@ -1484,7 +1491,7 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
         note_launch();
         k_warp_hash<<<std::min((L.n_warp_items + kHashWarps - 1) / kHashWarps, sms * 3), kHashThreads,
                       kHashWarps * 2 * kHashSlots * 4, st>>>(
-            L.graphs, L.warp_items, L.n_warp_items, L.queue);
+            L.graphs, L.warp_items, L.n_warp_items, L.queue, T.queue_chunk);
         BBC_CUDA_TRY(cudaGetLastError());
         profile_end(tok, st);
         BBC_TRY(end_side(st));

@@ -261,14 +261,17 @@ __device__ __forceinline__ void classify_one(const ClassifyParams &P, const int6
     const long long maxcount = deg < (long long)wl ? deg : (long long)wl;
     const int w = width_for_bound((unsigned long long)maxcount);
     const long long span = P.orient_low ? a : (long long)P.nS - 1 - a;
-    if (P.warp_tiles && span <= (long long)group_tile_endpoints(1, w)) {
+    // with 8-bit counters a table starts at an even endpoint, one slot early for an odd
+    // first endpoint, so it holds two endpoints less than its size to be safe
+    const long long slack = w == 0 ? 2 : 0;
+    if (P.warp_tiles && span + slack <= (long long)group_tile_endpoints(1, w)) {
         *kind = 3;
         *cw = w;
         *ntiles = 1;
         *groups = 1;
         return;
     }
-    if (P.warp_tiles && span <= (long long)group_tile_endpoints(kGroupWarps, w)) {
+    if (P.warp_tiles && span + slack <= (long long)group_tile_endpoints(kGroupWarps, w)) {
         *kind = 4;
         *cw = w;
         *ntiles = 1;
