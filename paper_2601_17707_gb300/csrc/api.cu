@@ -171,6 +171,23 @@ void dev_free(void *p, cudaStream_t st) {
     if (p) cudaFreeAsync(p, st);
 }
 
+size_t l2_bytes() {
+    static thread_local int dev_cached = -1;
+    static thread_local size_t bytes = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return (size_t)128 << 20;
+    if (dev != dev_cached) {
+        int v = 0;
+        bytes = cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev) == cudaSuccess && v > 0
+                    ? (size_t)v
+                    : (size_t)128 << 20;
+        dev_cached = dev;
+    }
+    return bytes;
+}
+
+bool rows_exceed_l2(const bbc_graph *g) { return (size_t)g->n_edges * 4 > l2_bytes(); }
+
 int device_sm_count() {
     PoolEntry *e = device_entry();
     if (e && e->sms > 0) return e->sms;
@@ -258,6 +275,7 @@ bbc_status count_graph(bbc_graph *g, uint64_t *totals_dev, uint64_t *per_u, uint
     L.n_gt_items = g->n_gt;
     L.queue = g->queue;
     L.tuning = T;
+    L.prefetch = rows_exceed_l2(g);
     BBC_TRY(launch_count(L, st));
     if (pv) {
         uint64_t *outS = g->side == 0 ? per_u : per_v;

@@ -293,6 +293,7 @@ bbc_status build_plan(int32_t n, bbc_graph *const *gs, const Tuning &T, std::uni
     L.n_gt_items = P->n_gt;
     L.queue = P->queue;
     L.tuning = T;
+    for (int i = 0; i < n; ++i) L.prefetch = L.prefetch || rows_exceed_l2(gs[i]);
     P->launch = L;
     BBC_TRY(configure_count_kernels());
     BBC_TRY(ensure_side_streams());   // no stream or event creation inside the capture

@@ -191,6 +191,7 @@ bbc_status dev_alloc_n(T **p, size_t n, cudaStream_t st) {
 }
 
 int device_sm_count();
+size_t l2_bytes();           // L2 size of the current device
 bbc_status check_device();   // the current device is usable (compute capability 10.3)
 
 // ----------------------------------------------------------------------------- sort/scan
@@ -221,6 +222,8 @@ struct CountLaunch {
     QueueState *queue;          // device, zeroed by the caller before the launch
     Tuning tuning;
     long long *item_cycles = nullptr;  // device, per tile item: its duration in SM cycles
+    bool prefetch = false;      // the graphs' C -> S rows are larger than L2: the tile kernel
+                                // asks for each slice's first lines ahead of use
 };
 
 // One contiguous run of a graph's work items to copy into a combined list, tagged with

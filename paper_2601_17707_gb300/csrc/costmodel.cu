@@ -567,6 +567,7 @@ bbc_status bbc_item_cycles(bbc_graph *g, int64_t *cycles_dev, int32_t capacity, 
         L.n_tile_items = g->n_tile;
         L.queue = g->queue;
         L.tuning = g->items_tuning;
+        L.prefetch = rows_exceed_l2(g);
         if (L.tuning.blocks_per_sm < 1) L.tuning.blocks_per_sm = 2;
         L.tuning.plain = 0;
         L.item_cycles = reinterpret_cast<long long *>(cycles_dev);

@@ -49,7 +49,7 @@ constexpr int kWtThreads = 512;          // warp-tile kernel: 16 warps, one tabl
 constexpr int kWtWarps = kWtThreads / 32;
 constexpr int kHashThreads = 256;
 constexpr int kHashWarps = kHashThreads / 32;
-constexpr int kHashSlots = 1024;          // per warp; holds anchors of <= 512 wedges
+constexpr int kHashSlots = 1024;          // most per warp; holds anchors of <= 512 wedges
 constexpr uint32_t kEmpty = 0xffffffffu;
 
 __device__ __forceinline__ int64_t lower_bound_rank(const uint32_t *__restrict__ row, int64_t b,
@@ -70,6 +70,11 @@ __device__ __forceinline__ int64_t lower_bound_rank(const uint32_t *__restrict__
 // its old value; the explicit reduction does not.
 __device__ __forceinline__ void red_add(unsigned long long *p, unsigned long long v) {
     asm volatile("red.global.add.u64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "l"(v) : "memory");
+}
+
+// A hint that brings a line of global memory into L2 (no register, no wait).
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p)));
 }
 
 __device__ __forceinline__ unsigned long long choose2(unsigned long long x) {
@@ -357,13 +362,6 @@ __device__ __forceinline__ unsigned long long block_exclusive_scan_u64(unsigned 
 template <int CW>
 using Acc = typename std::conditional<CW == 2, unsigned long long, uint32_t>::type;
 
-__device__ __forceinline__ uint32_t warp_sum32(uint32_t x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-    return x;
-}
-__device__ __forceinline__ unsigned long long warp_sum_acc(unsigned long long x) { return warp_sum(x); }
-__device__ __forceinline__ uint32_t warp_sum_acc(uint32_t x) { return warp_sum32(x); }
 
 // One wedge given by its C -> S entry x and the counter's sign key of the anchor edge:
 // MODE 0 bumps its counter; MODE 1 adds the counter's value to acc (the caller subtracts
@@ -655,7 +653,7 @@ __device__ __forceinline__ unsigned long long acc_get(ChunkSmem &cs, int j) {
 // coalesced 16-byte loads. MODE 0
 // bumps the counters; MODE 1 reads them and adds (count - 1) per wedge to the centre's
 // per-vertex sum. A single-chunk MODE 1 pass reuses the slices MODE 0 just found.
-template <int MODE, int CW, class Ctr>
+template <int MODE, int CW, class Ctr, bool PF = false>
 __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const SweepCtx &X,
                             const Ctr &ctr, ChunkSmem &cs, unsigned long long &centre_carry) {
     const int tid = threadIdx.x, lane = tid & 31;
@@ -672,6 +670,14 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
             if (ci < se) {
                 ent = __ldg(G.rowS + ci);
                 find_slice(G, ci, ci - sb, X, start, len);
+            }
+            // PF (graphs whose rows do not fit L2): each slice's first lines (all of a short
+            // slice: at most 64 entries, three 128-byte lines) are requested now, so that
+            // the sweep below finds them in L2
+            if (PF && len) {
+                prefetch_l2(G.rowC + start);
+                prefetch_l2(G.rowC + start + min(len - 1, 32u));
+                prefetch_l2(G.rowC + start + min(len - 1, 63u));
             }
             const bool islong = len >= (uint32_t)kLongMin;
             const uint32_t slen = islong ? 0u : len;
@@ -848,7 +854,7 @@ __device__ __forceinline__ void tile_epilogue(uint32_t *tile, uint32_t lo, uint3
     }
 }
 
-template <int CW>
+template <int CW, bool PF>
 __device__ void run_tile_item(const DevGraph &G, const TileItem &item, int tile_words, uint32_t *tile,
                               ChunkSmem &cs, unsigned long long &bal, unsigned long long &unb) {
     const int a = item.anchor;
@@ -868,8 +874,8 @@ __device__ void run_tile_item(const DevGraph &G, const TileItem &item, int tile_
         X.lo = X.range_lo + (uint32_t)t * ept;
         X.hi = min(X.lo + ept, X.range_hi);
         const BlockTile<CW> ctr(tile, X.lo);
-        block_sweep<0, CW>(G, sb, se, X, ctr, cs, centre_carry);
-        if (G.bC) block_sweep<1, CW>(G, sb, se, X, ctr, cs, centre_carry);
+        block_sweep<0, CW, BlockTile<CW>, PF>(G, sb, se, X, ctr, cs, centre_carry);
+        if (G.bC) block_sweep<1, CW, BlockTile<CW>, PF>(G, sb, se, X, ctr, cs, centre_carry);
         tile_epilogue<CW>(tile, BlockTile<CW>::origin(X.lo), X.hi, G.bS, bal, unb);
         __syncthreads();
     }
@@ -878,19 +884,20 @@ __device__ void run_tile_item(const DevGraph &G, const TileItem &item, int tile_
 
 // One tile [X.lo, X.hi) of an anchor: the count sweep, the centre sweep (per-vertex
 // counts), the epilogue.
-template <int CW>
+template <int CW, bool PF>
 __device__ void tile_pass(const DevGraph &G, int64_t sb, int64_t se, const SweepCtx &X, uint32_t *tile,
                           ChunkSmem &cs, unsigned long long &centre_carry, unsigned long long &bal,
                           unsigned long long &unb) {
     const BlockTile<CW> ctr(tile, X.lo);
-    block_sweep<0, CW>(G, sb, se, X, ctr, cs, centre_carry);
-    if (G.bC) block_sweep<1, CW>(G, sb, se, X, ctr, cs, centre_carry);
+    block_sweep<0, CW, BlockTile<CW>, PF>(G, sb, se, X, ctr, cs, centre_carry);
+    if (G.bC) block_sweep<1, CW, BlockTile<CW>, PF>(G, sb, se, X, ctr, cs, centre_carry);
     tile_epilogue<CW>(tile, BlockTile<CW>::origin(X.lo), X.hi, G.bS, bal, unb);
     __syncthreads();
 }
 
 // An item whose tiles choose their counter width one by one (the tile boundaries are the
 // same walk that preparation used for the boundary table).
+template <bool PF>
 __device__ void run_tile_item_var(const DevGraph &G, const TileItem &item, int tile_words, uint32_t *tile,
                                   ChunkSmem &cs, unsigned long long &bal, unsigned long long &unb) {
     const int a = item.anchor;
@@ -913,16 +920,18 @@ __device__ void run_tile_item_var(const DevGraph &G, const TileItem &item, int t
         X.lo = vt.lo;
         X.hi = vt.hi;
         switch (vt.cw) {
-            case 0: tile_pass<0>(G, sb, se, X, tile, cs, centre_carry, bal, unb); break;
-            case 1: tile_pass<1>(G, sb, se, X, tile, cs, centre_carry, bal, unb); break;
-            default: tile_pass<2>(G, sb, se, X, tile, cs, centre_carry, bal, unb); break;
+            case 0: tile_pass<0, PF>(G, sb, se, X, tile, cs, centre_carry, bal, unb); break;
+            case 1: tile_pass<1, PF>(G, sb, se, X, tile, cs, centre_carry, bal, unb); break;
+            default: tile_pass<2, PF>(G, sb, se, X, tile, cs, centre_carry, bal, unb); break;
         }
         if (t + 1 < t1) vt = var_tile_at(G.rowS_off, bound, vt.hi, X.range_hi, (uint32_t)tile_words);
     }
     if (centre_carry) red_add(G.bC + (cs.ent[threadIdx.x] & kIdMask), centre_carry);
 }
 
-// Persistent blocks pop (anchor, tile range) items, heaviest first.
+// Persistent blocks pop (anchor, tile range) items, heaviest first. PF: the graphs' rows
+// are much larger than L2 (slices are prefetched into L2 as their chunk is set up).
+template <bool PF>
 __global__ void __launch_bounds__(kTileThreads, 2)
 k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, int n_items,
        unsigned *head, int tile_words, int static_schedule, long long *item_cycles) {
@@ -951,10 +960,10 @@ k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, 
         const long long t_start = item_cycles ? clock64() : 0;
         unsigned long long bal = 0, unb = 0;
         switch (tile_width_of(item)) {
-            case 0: run_tile_item<0>(G, item, tile_words, tile, cs, bal, unb); break;
-            case 1: run_tile_item<1>(G, item, tile_words, tile, cs, bal, unb); break;
-            case 2: run_tile_item<2>(G, item, tile_words, tile, cs, bal, unb); break;
-            default: run_tile_item_var(G, item, tile_words, tile, cs, bal, unb); break;
+            case 0: run_tile_item<0, PF>(G, item, tile_words, tile, cs, bal, unb); break;
+            case 1: run_tile_item<1, PF>(G, item, tile_words, tile, cs, bal, unb); break;
+            case 2: run_tile_item<2, PF>(G, item, tile_words, tile, cs, bal, unb); break;
+            default: run_tile_item_var<PF>(G, item, tile_words, tile, cs, bal, unb); break;
         }
         bal = warp_sum(bal);
         unb = warp_sum(unb);
@@ -980,15 +989,18 @@ k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, 
 
 __global__ void __launch_bounds__(kHashThreads)
 k_warp_hash(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ items, int n_items,
-            QueueState *q, int chunk) {
+            QueueState *q, int chunk, int slots_lg) {
     extern __shared__ uint4 smem_hash[];
     __shared__ uint32_t s_acc[kHashWarps][32];
     __shared__ int s_batch[kHashWarps];
     __shared__ WarpStage s_stage[kHashWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *keys = reinterpret_cast<uint32_t *>(smem_hash) + warp * 2 * kHashSlots;
-    uint32_t *vals = keys + kHashSlots;
-    for (int i = lane; i < kHashSlots; i += 32) {
+    // each warp's table holds 2^slots_lg slots: twice the largest wedge count of the
+    // launch's items, so that small tables leave room for more resident warps
+    const int slots = 1 << slots_lg;
+    uint32_t *keys = reinterpret_cast<uint32_t *>(smem_hash) + warp * 2 * slots;
+    uint32_t *vals = keys + slots;
+    for (int i = lane; i < slots; i += 32) {
         keys[i] = kEmpty;
         vals[i] = 0;
     }
@@ -1009,7 +1021,7 @@ k_warp_hash(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ it
         const int64_t sb = G.rowS_off[a], se = G.rowS_off[a + 1];
         // table of 2^k >= 2 * wedges slots (at least 64)
         int lg = 6;
-        while ((1 << lg) < 2 * item.wedges && lg < 10) ++lg;
+        while ((1 << lg) < 2 * item.wedges && lg < slots_lg) ++lg;
         const HashCounter ctr{keys, vals, (1u << lg) - 1u, 32 - lg, &q->error};
         if (lane == 0) s_batch[warp] = 0;
         __syncwarp();
@@ -1358,15 +1370,17 @@ bbc_status configure_count_kernels() {
     BBC_CUDA_TRY(cudaGetDevice(&dev));
     if (configured_device != dev) {
         cudaFuncAttributes fa{};
-        BBC_CUDA_TRY(cudaFuncGetAttributes(&fa, k_tile));
-        if ((int)fa.sharedSizeBytes > tile_static_smem_bytes()) {
-            set_error("tile kernel static shared memory exceeds its budget");
-            return BBC_E_CUDA;
-        }
         int maxopt = 0;
         BBC_CUDA_TRY(cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        BBC_CUDA_TRY(cudaFuncSetAttribute(k_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          maxopt - (int)fa.sharedSizeBytes));
+        for (const void *f : {(const void *)k_tile<false>, (const void *)k_tile<true>}) {
+            BBC_CUDA_TRY(cudaFuncGetAttributes(&fa, f));
+            if ((int)fa.sharedSizeBytes > tile_static_smem_bytes()) {
+                set_error("tile kernel static shared memory exceeds its budget");
+                return BBC_E_CUDA;
+            }
+            BBC_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              maxopt - (int)fa.sharedSizeBytes));
+        }
         for (const void *f : {(const void *)k_tile_motif<1>, (const void *)k_tile_motif<2>}) {
             cudaFuncAttributes fm{};
             BBC_CUDA_TRY(cudaFuncGetAttributes(&fm, f));
@@ -1423,6 +1437,28 @@ bbc_status ensure_side_streams() {
     return side_streams(ss);
 }
 
+// Resident blocks per SM of the hash kernel with tables of 2^slots_lg slots per warp
+// (the occupancy calculator's answer, kept per device and table size).
+int hash_blocks_per_sm(int slots_lg) {
+    static thread_local int dev_cached = -1;
+    static thread_local int occ[11] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 3;
+    if (dev != dev_cached) {
+        for (int &o : occ) o = 0;
+        dev_cached = dev;
+    }
+    if (occ[slots_lg] == 0) {
+        int nb = 0;
+        const size_t smem = (size_t)kHashWarps * 2 * ((size_t)1 << slots_lg) * 4;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_warp_hash, kHashThreads, smem) != cudaSuccess ||
+            nb < 1)
+            nb = 3;
+        occ[slots_lg] = nb;
+    }
+    return occ[slots_lg];
+}
+
 bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
     BBC_TRY(configure_count_kernels());
     const int sms = device_sm_count();
@@ -1433,7 +1469,8 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
         // work-queue schedule: persistent blocks (no more than there are items); plain
         // schedule: one block per item
         const int grid = T.plain ? L.n_tile_items : std::min(L.n_tile_items, sms * T.blocks_per_sm);
-        k_tile<<<grid, kTileThreads, (size_t)(T.tile_words + kTileSlackWords) * 4, st>>>(
+        auto kern = L.prefetch ? k_tile<true> : k_tile<false>;
+        kern<<<grid, kTileThreads, (size_t)(T.tile_words + kTileSlackWords) * 4, st>>>(
             L.graphs, L.tile_items, L.n_tile_items, &L.queue->tile_head, T.tile_words, T.plain,
             L.item_cycles);
         BBC_CUDA_TRY(cudaGetLastError());
@@ -1489,9 +1526,12 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
         cudaStream_t st = begin_side();
         const int tok = profile_begin(kProfHash, st);
         note_launch();
-        k_warp_hash<<<std::min((L.n_warp_items + kHashWarps - 1) / kHashWarps, sms * 3), kHashThreads,
-                      kHashWarps * 2 * kHashSlots * 4, st>>>(
-            L.graphs, L.warp_items, L.n_warp_items, L.queue, T.queue_chunk);
+        int slots_lg = 6;
+        while ((1 << slots_lg) < 2 * T.warp_max_wedges && slots_lg < 10) ++slots_lg;
+        const size_t smem = (size_t)kHashWarps * 2 * ((size_t)1 << slots_lg) * 4;
+        k_warp_hash<<<std::min((L.n_warp_items + kHashWarps - 1) / kHashWarps, sms * hash_blocks_per_sm(slots_lg)),
+                      kHashThreads, smem, st>>>(L.graphs, L.warp_items, L.n_warp_items, L.queue,
+                                                T.queue_chunk, slots_lg);
         BBC_CUDA_TRY(cudaGetLastError());
         profile_end(tok, st);
         BBC_TRY(end_side(st));
@@ -1523,7 +1563,7 @@ bbc_status launch_tile_only(const DevGraph *graphs, const TileItem *items, int n
     BBC_TRY(configure_count_kernels());
     if (n_items <= 0) return BBC_OK;
     note_launch();
-    k_tile<<<blocks, kTileThreads, (size_t)(tile_words + kTileSlackWords) * 4, st>>>(graphs, items, n_items, head,
+    k_tile<false><<<blocks, kTileThreads, (size_t)(tile_words + kTileSlackWords) * 4, st>>>(graphs, items, n_items, head,
                                                                  tile_words, 0, nullptr);
     BBC_CUDA_TRY(cudaGetLastError());
     return BBC_OK;

@@ -61,5 +61,7 @@ void release_graph(bbc_graph *g, cudaStream_t st);
 // The kernels' view of g. with_bounds: the tile boundaries of the work lists last
 // built (pass true only right after build_work_lists with the tuning being launched).
 DevGraph host_descriptor(const bbc_graph *g, bool per_vertex, bool with_bounds = false);
+// The graph's C -> S rows (4 bytes per edge) are larger than the device's L2.
+bool rows_exceed_l2(const bbc_graph *g);
 
 }  // namespace bbc

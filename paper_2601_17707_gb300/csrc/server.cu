@@ -272,6 +272,7 @@ bbc_status run_tick(bbc_server *S, std::vector<Request *> &act) {
     L.n_gt_items = (int32_t)ngr;
     L.queue = S->queue_state;
     L.tuning = S->tuning;
+    for (size_t i = 0; i < n; ++i) L.prefetch = L.prefetch || rows_exceed_l2(act[i]->g);
     BBC_CUDA_TRY(cudaEventRecord(S->ev_a, st));
     BBC_TRY(launch_count(L, st));
     BBC_CUDA_TRY(cudaEventRecord(S->ev_b, st));
