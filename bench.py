@@ -44,7 +44,7 @@ METRIC = "wedges/sec & % HBM roofline; batched graphs/sec vs per-graph launches"
 UNIT = "wedges/s"
 WORKLOAD = "powerlaw_1m_200k_20m"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_tile_powerlaw_1m_200k_20m.traffic.json")
+TRAFFIC_DIR = os.path.join(ROOT, "profiles")
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -111,12 +111,11 @@ def kernel_source_digest() -> str:
 
 
 def recorded_traffic(workload: str = WORKLOAD):
-    """Per-launch DRAM bytes of the tile kernel from the committed ncu summary, or None
-    when the kernel source changed since that capture (or for another workload)."""
-    if workload != WORKLOAD:
-        return None
+    """Per-launch DRAM bytes of the tile kernel from the committed ncu summary of this
+    workload (profiles/k_tile_<workload>.traffic.json), or None when there is none or the
+    kernel source changed since that capture."""
     try:
-        with open(TRAFFIC_FILE) as f:
+        with open(os.path.join(TRAFFIC_DIR, f"k_tile_{workload}.traffic.json")) as f:
             rec = json.load(f)
     except Exception:
         return None

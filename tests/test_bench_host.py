@@ -26,9 +26,9 @@ def test_code_only_drops_comments_and_keeps_strings():
 
 def test_traffic_record_follows_the_kernel_digest(tmp_path, monkeypatch):
     rec = {"dram_bytes_per_launch": 123.0, "source_sha256": bench.kernel_source_digest()}
-    path = tmp_path / "traffic.json"
+    path = tmp_path / f"k_tile_{bench.WORKLOAD}.traffic.json"
     path.write_text(json.dumps(rec))
-    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(path))
+    monkeypatch.setattr(bench, "TRAFFIC_DIR", str(tmp_path))
     assert bench.recorded_traffic() == 123.0
     assert bench.recorded_traffic("uniform_2k_3k") is None
     path.write_text(json.dumps(dict(rec, source_sha256="0" * 64)))
