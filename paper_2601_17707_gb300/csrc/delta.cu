@@ -7,16 +7,17 @@
 // f(p, n) = C(p,2) + C(n,2) (and p * n), where p and n count the common neighbours
 // reached by symmetric and asymmetric wedges. A pair's (p, n) changes only through an
 // edge (a, c) or (w, c) in D, so only pairs with a member in A, the set of S vertices that
-// an update touches, can change. For every a in A one block recounts a's pair vector in
-// G and in G' (all endpoints w, no orientation), and each pair {a, w} adds
-// f(G') - f(G) once: at a when w is outside A or ranks above a.
+// an update touches, can change. For every a in A the pair vector of a is recounted in G
+// and in G' (all endpoints w, no orientation), one endpoint tile per block at a time, and
+// each pair {a, w} adds f(G') - f(G) once: at a when w is outside A or ranks above a.
 //
 // Steps: ids -> ranks (k_rank_of); updates -> (a, c, old sign from the CSR, new sign)
 // with range and sign checks (k_map_updates); stable radix sorts by a and by (c, a);
 // duplicate and absent-deletion checks (k_check_updates); the distinct anchors A
-// (k_anchor_marks + scan); one block per anchor of A (k_delta_anchor), which adds into
-// four global counters per endpoint (short centre rows a warp each, long ones the whole
-// block) and then reads and clears the whole counter array.
+// (k_anchor_marks + scan); work items (anchor, endpoint tile), heaviest anchors first
+// (k_delta_plan, a radix sort, a scan); persistent blocks over the items (k_delta_tile),
+// each with a shared-memory tile of four counters per endpoint (old p, old n, new p,
+// new n) that the anchor's centre rows fill and the tile's epilogue turns into changes.
 #include "graph.cuh"
 
 namespace bbc {
@@ -162,54 +163,16 @@ struct DeltaArgs {
     const uint32_t *anchors, *seg_begin;
     int32_t n_anchors;
     const uint8_t *in_a;
-    // per block scratch: 4 counters (old p, old n, new p, new n) per endpoint, zero
-    // between anchors
-    uint32_t *cnt;
-    unsigned *next_anchor;
+    // work items: anchor k (in the order `order`) owns items toff[k] .. toff[k + 1] - 1,
+    // one per endpoint tile; cw[k] is its counter width code
+    const uint32_t *order;
+    const int64_t *toff;
+    const uint8_t *cw;
+    int64_t n_items;
+    int32_t tile_words;
+    unsigned *next_item;
     unsigned long long *out;   // [0] delta balanced, [1] delta unbalanced (two's complement)
 };
-
-__device__ __forceinline__ void touch(uint32_t *cnt, uint32_t w, int slot) {
-    atomicAdd(cnt + 4 * (size_t)w + slot, 1u);
-}
-
-// One centre c of anchor a: its old row, with every entry's new sign looked up among the
-// updates, then the insertions at c. Threads t, t + step, ... of the caller's group share
-// the row.
-__device__ void delta_centre(const DeltaArgs &A, uint32_t a, uint32_t c, uint32_t oa, uint32_t na,
-                             uint32_t *cnt, int t, int step) {
-    const int64_t b = A.rowC_off[c], e = A.rowC_off[c + 1];
-    const int64_t u0 = lower_key(A.key, A.n_upd, (unsigned long long)c << 32);
-    const int64_t u1 = lower_key(A.key, A.n_upd, ((unsigned long long)c + 1) << 32);
-    for (int64_t j = b + t; j < e; j += step) {
-        const uint32_t x = A.rowC[j];
-        const uint32_t w = x & kIdMask;
-        if (w == a) continue;
-        const uint32_t ow = (x >> 31) ? 2u : 1u;
-        uint32_t nw = ow;
-        if (u1 > u0) {   // an update at this centre may re-sign or delete (w, c)
-            int64_t lo = u0, hi = u1;
-            const unsigned long long k = ((unsigned long long)c << 32) | w;
-            while (lo < hi) {
-                const int64_t m = (lo + hi) >> 1;
-                if (A.key[m] < k)
-                    lo = m + 1;
-                else
-                    hi = m;
-            }
-            if (lo < u1 && A.key[lo] == k) nw = A.knew[lo];
-        }
-        if (oa && ow) touch(cnt, w, oa == ow ? 0 : 1);
-        if (na && nw) touch(cnt, w, na == nw ? 2 : 3);
-    }
-    if (na)
-        for (int64_t q = u0 + t; q < u1; q += step) {
-            if (A.kold[q] != kAbsent || A.knew[q] == kAbsent) continue;   // insertions only
-            const uint32_t w = (uint32_t)(A.key[q] & 0xffffffffull);
-            if (w == a) continue;
-            touch(cnt, w, na == A.knew[q] ? 2 : 3);
-        }
-}
 
 // The new sign code of edge (a, c) given its old one.
 __device__ __forceinline__ uint32_t new_code(const DeltaArgs &A, uint32_t a, uint32_t c, uint32_t oa) {
@@ -218,64 +181,212 @@ __device__ __forceinline__ uint32_t new_code(const DeltaArgs &A, uint32_t a, uin
     return (q < A.n_upd && A.key[q] == k) ? A.knew[q] : oa;
 }
 
-constexpr int64_t kLongRow = 1024;   // centre rows this long are swept by the whole block
+// First index of row[b, e) whose rank is >= key.
+__device__ __forceinline__ int64_t lower_rank(const uint32_t *__restrict__ row, int64_t b, int64_t e, uint32_t key) {
+    while (b < e) {
+        const int64_t m = (b + e) >> 1;
+        if ((row[m] & kIdMask) < key)
+            b = m + 1;
+        else
+            e = m;
+    }
+    return b;
+}
 
-__global__ void __launch_bounds__(kDeltaThreads) k_delta_anchor(DeltaArgs A) {
-    __shared__ int s_item;
-    __shared__ long long s_red[2][kDeltaWarps];
-    uint32_t *cnt = A.cnt + (size_t)blockIdx.x * 4 * (size_t)A.nS;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Anchor k's counter width: a pair's old or new count is at most the anchor's number of
+// centres before or after the batch.
+__global__ void k_delta_plan(DeltaArgs A, const uint32_t *__restrict__ seg_end, int32_t *__restrict__ ntiles,
+                             uint8_t *__restrict__ cw, uint32_t *__restrict__ deg_key) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < A.n_anchors;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = A.anchors[k];
+        const int64_t deg = A.rowS_off[a + 1] - A.rowS_off[a];
+        const int64_t bound = deg + (int64_t)(seg_end[k] - A.seg_begin[k]);
+        const int w = bound <= 255 ? 0 : (bound <= 65535 ? 1 : 2);
+        const int64_t ept = (int64_t)A.tile_words >> w;   // 1, 2 or 4 words per endpoint
+        cw[k] = (uint8_t)w;
+        ntiles[k] = (int32_t)((A.nS + ept - 1) / ept);
+        // heaviest anchors first: the sort key is the complement of the degree
+        deg_key[k] = 0xffffffffu - (uint32_t)(bound < 0xffffffffll ? bound : 0xffffffffll);
+    }
+}
+
+constexpr int kDeltaTileThreads = 512;
+constexpr int kDeltaTileWarps = kDeltaTileThreads / 32;
+
+// Per chunk of up to 512 centres of an item's anchor: the slice of each centre's row in
+// the item's endpoint tile, its old / new anchor-edge codes and its range of updates.
+struct DeltaChunk {
+    uint32_t c[kDeltaTileThreads];
+    uint32_t s[kDeltaTileThreads], e[kDeltaTileThreads];
+    uint32_t u0[kDeltaTileThreads], u1[kDeltaTileThreads];
+    uint8_t codes[kDeltaTileThreads];
+};
+
+// One counter of endpoint w (relative rank e) in slot 0 (old, symmetric), 1 (old,
+// asymmetric), 2 (new, symmetric) or 3 (new, asymmetric).
+__device__ __forceinline__ void delta_bump(uint32_t *tile, int cw, uint32_t e, uint32_t slot) {
+    if (cw == 0)
+        atomicAdd(tile + e, 1u << (8 * slot));
+    else if (cw == 1)
+        atomicAdd(tile + 2 * e + (slot >> 1), 1u << (16 * (slot & 1)));
+    else
+        atomicAdd(tile + 4 * e + slot, 1u);
+}
+
+// Persistent blocks pop (anchor, endpoint tile) items. For its tile [lo, hi) a block
+// finds, chunk by chunk, the slice of every centre row of the anchor (old centres from the
+// S -> C row, inserted ones from the update list) with two binary searches, and its warps
+// sweep the slices 32 entries at a time: an entry (w, c) bumps the old counter of w by the
+// old codes and the new counter by the new ones (the entry's new code found among the
+// updates at c, when c has any), and the insertions at c inside the tile bump new
+// counters. The tile's counters then give every pair's change, counted once: at a unless
+// w is touched too and ranks below a.
+__global__ void __launch_bounds__(kDeltaTileThreads, 2) k_delta_tile(DeltaArgs A) {
+    extern __shared__ uint4 smem_delta[];
+    uint32_t *tile = reinterpret_cast<uint32_t *>(smem_delta);
+    __shared__ DeltaChunk ch;
+    __shared__ long long s_item;
+    __shared__ long long s_red[2][kDeltaTileWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < A.tile_words; i += blockDim.x) tile[i] = 0;
     long long db = 0, du = 0;
     for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(A.next_anchor, 1u);
         __syncthreads();
-        const int it = s_item;
-        if (it >= A.n_anchors) break;
-        const uint32_t a = A.anchors[it];
-        const uint32_t sb = A.seg_begin[it];
-        const uint32_t se = it + 1 < A.n_anchors ? A.seg_begin[it + 1] : (uint32_t)A.n_upd;
+        if (tid == 0) s_item = (long long)atomicAdd(A.next_item, 1u);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= A.n_items) break;
+        // the item's anchor: the last k with toff[k] <= item
+        int lo_k = 0, hi_k = A.n_anchors - 1;
+        while (lo_k < hi_k) {
+            const int mid = (lo_k + hi_k + 1) >> 1;
+            if (A.toff[mid] <= item)
+                lo_k = mid;
+            else
+                hi_k = mid - 1;
+        }
+        const int k = (int)A.order[lo_k];
+        const int cw = A.cw[k];
+        const uint32_t a = A.anchors[k];
+        const int64_t ept = (int64_t)A.tile_words >> cw;
+        const uint32_t lo = (uint32_t)((item - A.toff[lo_k]) * ept);
+        const uint32_t hi = (uint32_t)((int64_t)lo + ept < A.nS ? (int64_t)lo + ept : A.nS);
+        const uint32_t sb = A.seg_begin[k];
+        const uint32_t se = k + 1 < A.n_anchors ? A.seg_begin[k + 1] : (uint32_t)A.n_upd;
         const int64_t rb = A.rowS_off[a], re = A.rowS_off[a + 1];
-        // short centre rows: a warp each
-        for (int64_t i = rb + warp; i < re; i += kDeltaWarps) {
-            const uint32_t x = A.rowS[i];
-            const uint32_t c = x & kIdMask;
-            if (A.rowC_off[c + 1] - A.rowC_off[c] >= kLongRow) continue;
-            const uint32_t oa = (x >> 31) ? 2u : 1u;
-            delta_centre(A, a, c, oa, new_code(A, a, c, oa), cnt, lane, 32);
+        const int64_t ncent = (re - rb) + (int64_t)(se - sb);   // old centres, then the updates
+        for (int64_t cb = 0; cb < ncent; cb += kDeltaTileThreads) {
+            const int64_t i = cb + tid;
+            uint32_t c = 0, codes = 0, s0 = 0, s1 = 0, q0 = 0, q1 = 0;
+            if (i < ncent) {
+                uint32_t oa = kAbsent, na = kAbsent;
+                bool use = true;
+                if (i < re - rb) {
+                    const uint32_t x = A.rowS[rb + i];
+                    c = x & kIdMask;
+                    oa = (x >> 31) ? 2u : 1u;
+                    na = new_code(A, a, c, oa);
+                } else {
+                    const uint32_t q = sb + (uint32_t)(i - (re - rb));
+                    c = A.c_by_a[q];
+                    // inserted centres only (the others are old centres already)
+                    use = A.old_by_a[q] == kAbsent && A.new_by_a[q] != kAbsent;
+                    na = A.new_by_a[q];
+                }
+                if (use) {
+                    const int64_t b = A.rowC_off[c], e = A.rowC_off[c + 1];
+                    const int64_t p0 = lower_rank(A.rowC, b, e, lo);
+                    s0 = (uint32_t)p0;
+                    s1 = (uint32_t)lower_rank(A.rowC, p0, e, hi);
+                    q0 = (uint32_t)lower_key(A.key, A.n_upd, (unsigned long long)c << 32);
+                    q1 = (uint32_t)lower_key(A.key, A.n_upd, ((unsigned long long)c + 1) << 32);
+                    codes = oa | (na << 2);
+                }
+            }
+            ch.c[tid] = c;
+            ch.s[tid] = s0;
+            ch.e[tid] = s1;
+            ch.u0[tid] = q0;
+            ch.u1[tid] = q1;
+            ch.codes[tid] = (uint8_t)codes;
+            __syncthreads();
+            const int nc = (int)(ncent - cb < kDeltaTileThreads ? ncent - cb : kDeltaTileThreads);
+            for (int j = warp; j < nc; j += kDeltaTileWarps) {
+                const uint32_t codes_j = ch.codes[j];
+                if (!codes_j) continue;
+                const uint32_t oa = codes_j & 3u, na = codes_j >> 2, cj = ch.c[j];
+                const uint32_t u0 = ch.u0[j], u1 = ch.u1[j];
+                // the old row's entries inside the tile
+                for (uint32_t p = ch.s[j] + lane; p < ch.e[j]; p += 32) {
+                    const uint32_t x = A.rowC[p];
+                    const uint32_t w = x & kIdMask;
+                    if (w == a) continue;
+                    const uint32_t ow = (x >> 31) ? 2u : 1u;
+                    uint32_t nw = ow;
+                    if (u1 > u0) {   // an update at this centre may re-sign or delete (w, c)
+                        const unsigned long long kk = ((unsigned long long)cj << 32) | w;
+                        uint32_t l = u0, h = u1;
+                        while (l < h) {
+                            const uint32_t m = (l + h) >> 1;
+                            if (A.key[m] < kk)
+                                l = m + 1;
+                            else
+                                h = m;
+                        }
+                        if (l < u1 && A.key[l] == kk) nw = A.knew[l];
+                    }
+                    if (oa && ow) delta_bump(tile, cw, w - lo, oa == ow ? 0u : 1u);
+                    if (na && nw) delta_bump(tile, cw, w - lo, na == nw ? 2u : 3u);
+                }
+                // insertions at this centre inside the tile
+                if (na && u1 > u0) {
+                    for (uint32_t q = u0 + lane; q < u1; q += 32) {
+                        const uint32_t w = (uint32_t)(A.key[q] & 0xffffffffull);
+                        if (w < lo || w >= hi || w == a) continue;
+                        if (A.kold[q] != kAbsent || A.knew[q] == kAbsent) continue;
+                        delta_bump(tile, cw, w - lo, na == A.knew[q] ? 2u : 3u);
+                    }
+                }
+            }
+            __syncthreads();
         }
-        for (uint32_t q = sb + warp; q < se; q += kDeltaWarps) {
-            const uint32_t c = A.c_by_a[q];
-            if (A.old_by_a[q] == kAbsent && A.new_by_a[q] != kAbsent &&
-                A.rowC_off[c + 1] - A.rowC_off[c] < kLongRow)
-                delta_centre(A, a, c, kAbsent, A.new_by_a[q], cnt, lane, 32);
-        }
-        // long centre rows: the whole block each
-        for (int64_t i = rb; i < re; ++i) {
-            const uint32_t x = A.rowS[i];
-            const uint32_t c = x & kIdMask;
-            if (A.rowC_off[c + 1] - A.rowC_off[c] < kLongRow) continue;
-            const uint32_t oa = (x >> 31) ? 2u : 1u;
-            delta_centre(A, a, c, oa, new_code(A, a, c, oa), cnt, threadIdx.x, kDeltaThreads);
-        }
-        for (uint32_t q = sb; q < se; ++q) {
-            const uint32_t c = A.c_by_a[q];
-            if (A.old_by_a[q] == kAbsent && A.new_by_a[q] != kAbsent &&
-                A.rowC_off[c + 1] - A.rowC_off[c] >= kLongRow)
-                delta_centre(A, a, c, kAbsent, A.new_by_a[q], cnt, threadIdx.x, kDeltaThreads);
-        }
-        __syncthreads();
-        // every endpoint's four counters, read 16 bytes at a time, then cleared
-        uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
-        for (int64_t w = threadIdx.x; w < A.nS; w += kDeltaThreads) {
-            const uint4 k4 = c4[w];
-            if ((k4.x | k4.y | k4.z | k4.w) == 0) continue;
-            c4[w] = make_uint4(0u, 0u, 0u, 0u);
-            if (A.in_a[w] && (uint32_t)w < a) continue;   // the pair is counted at w
-            const long long po = k4.x, no = k4.y, pn = k4.z, nn = k4.w;
+        // the tile's pairs: change of f = C(p,2) + C(n,2) and of p * n; then cleared
+        const uint32_t n = hi - lo;
+        const uint32_t wpe = 1u << cw;
+        for (uint32_t e = tid; e < n; e += kDeltaTileThreads) {
+            uint32_t cnt[4];
+            if (cw == 0) {
+                const uint32_t v = tile[e];
+                if (!v) continue;
+                tile[e] = 0;
+                cnt[0] = v & 0xffu;
+                cnt[1] = (v >> 8) & 0xffu;
+                cnt[2] = (v >> 16) & 0xffu;
+                cnt[3] = v >> 24;
+            } else if (cw == 1) {
+                const uint32_t v0 = tile[2 * e], v1 = tile[2 * e + 1];
+                if (!(v0 | v1)) continue;
+                tile[2 * e] = 0;
+                tile[2 * e + 1] = 0;
+                cnt[0] = v0 & 0xffffu;
+                cnt[1] = v0 >> 16;
+                cnt[2] = v1 & 0xffffu;
+                cnt[3] = v1 >> 16;
+            } else {
+                uint32_t *q = tile + wpe * e;
+                if (!(q[0] | q[1] | q[2] | q[3])) continue;
+                for (int t = 0; t < 4; ++t) {
+                    cnt[t] = q[t];
+                    q[t] = 0;
+                }
+            }
+            const uint32_t w = lo + e;
+            if (A.in_a[w] && w < a) continue;   // the pair is counted at w
+            const long long po = cnt[0], no = cnt[1], pn = cnt[2], nn = cnt[3];
             db += (pn * (pn - 1) / 2 + nn * (nn - 1) / 2) - (po * (po - 1) / 2 + no * (no - 1) / 2);
             du += pn * nn - po * no;
         }
-        __syncthreads();
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -287,15 +398,28 @@ __global__ void __launch_bounds__(kDeltaThreads) k_delta_anchor(DeltaArgs A) {
         s_red[1][warp] = du;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         long long b = 0, u = 0;
-        for (int w = 0; w < kDeltaWarps; ++w) {
+        for (int w = 0; w < kDeltaTileWarps; ++w) {
             b += s_red[0][w];
             u += s_red[1][w];
         }
         if (b) atomicAdd(A.out, (unsigned long long)b);
         if (u) atomicAdd(A.out + 1, (unsigned long long)u);
     }
+}
+
+__global__ void k_seg_end(const uint32_t *__restrict__ seg_begin, int32_t n_anchors, int64_t n_upd,
+                          uint32_t *__restrict__ seg_end) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_anchors;
+         k += (int64_t)gridDim.x * blockDim.x)
+        seg_end[k] = k + 1 < n_anchors ? seg_begin[k + 1] : (uint32_t)n_upd;
+}
+
+__global__ void k_gather_i32(const int32_t *__restrict__ src, const uint32_t *__restrict__ order, int64_t n,
+                             int32_t *__restrict__ dst) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[order[i]];
 }
 
 // Device buffers released together when the owner leaves scope.
@@ -323,6 +447,20 @@ unsigned grid_n(int64_t n) {
     int64_t b = (n + 255) / 256;
     const int64_t cap = (int64_t)device_sm_count() * 16;
     return (unsigned)std::max<int64_t>(1, std::min(b, cap));
+}
+
+// The delta tile kernel's dynamic shared memory limit (its counter tile) on the current
+// device.
+bbc_status configure_delta_kernel(int tile_words) {
+    static thread_local int configured = -1;
+    int dev = 0;
+    BBC_CUDA_TRY(cudaGetDevice(&dev));
+    if (configured != dev) {
+        BBC_CUDA_TRY(cudaFuncSetAttribute(k_delta_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          tile_words * 4));
+        configured = dev;
+    }
+    return BBC_OK;
 }
 
 int bits_for(int64_t n) {
@@ -467,18 +605,42 @@ extern "C" bbc_status bbc_count_delta(const bbc_graph *g, int64_t n_updates, con
             set_error("bbc_count_delta: a deletion of an edge the graph does not hold");
             return BBC_E_INVALID_ARG;
         }
-        // per-block scratch: 16 bytes per pair-side vertex, at most ~4 GB in all
-        const int64_t per_block = 16 * std::max<int64_t>(nS, 1);
-        int64_t blocks = std::min<int64_t>(n_anchors, (int64_t)device_sm_count() * 2);
-        blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, ((int64_t)4 << 30) / per_block));
-        uint32_t *cnt = nullptr;
-        BBC_TRY(B.get(&cnt, (size_t)blocks * 4 * (size_t)std::max<int64_t>(nS, 1)));
-        BBC_CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)blocks * 16 * (size_t)std::max<int64_t>(nS, 1), st));
+        // work items: one per (anchor, endpoint tile), heaviest anchors first
+        if (n_anchors == 0) return BBC_OK;
+        const int32_t na = (int32_t)n_anchors;
+        uint32_t *seg_end = nullptr, *deg_key = nullptr, *order = nullptr;
+        int32_t *ntiles = nullptr, *ntiles_sorted = nullptr;
+        int64_t *toff = nullptr;
+        uint8_t *cw = nullptr;
+        BBC_TRY(B.get(&seg_end, (size_t)na));
+        BBC_TRY(B.get(&deg_key, (size_t)na));
+        BBC_TRY(B.get(&order, (size_t)na));
+        BBC_TRY(B.get(&ntiles, (size_t)na));
+        BBC_TRY(B.get(&ntiles_sorted, (size_t)na));
+        BBC_TRY(B.get(&toff, (size_t)na + 1));
+        BBC_TRY(B.get(&cw, (size_t)na));
+        const Tuning T = resolve_tuning(nullptr, device_sm_count());
         DeltaArgs A{g->rowS_off, g->rowS, g->rowC_off, g->rowC, nS, key, kold, knew, n,
-                    c_by_a, old_by_a, new_by_a, anchors, seg, (int32_t)n_anchors, in_a,
-                    cnt, next, out};
+                    c_by_a, old_by_a, new_by_a, anchors, seg, na, in_a,
+                    order, toff, cw, 0, T.tile_words, next, out};
         note_launch();
-        k_delta_anchor<<<(unsigned)blocks, kDeltaThreads, 0, st>>>(A);
+        k_seg_end<<<grid_n(na), 256, 0, st>>>(seg, na, n, seg_end);
+        note_launch();
+        k_delta_plan<<<grid_n(na), 256, 0, st>>>(A, seg_end, ntiles, cw, deg_key);
+        note_launch();
+        k_iota_u32<<<grid_n(na), 256, 0, st>>>(order, na);
+        BBC_TRY(radix_sort_pairs(deg_key, order, na, 32, st));
+        note_launch();
+        k_gather_i32<<<grid_n(na), 256, 0, st>>>(ntiles, order, na, ntiles_sorted);
+        BBC_TRY(exclusive_scan_i32_to_i64(ntiles_sorted, toff, na, st));
+        int64_t n_items = 0;
+        BBC_CUDA_TRY(cudaMemcpyAsync(&n_items, toff + na, 8, cudaMemcpyDeviceToHost, st));
+        BBC_CUDA_TRY(cudaStreamSynchronize(st));
+        A.n_items = n_items;
+        BBC_TRY(configure_delta_kernel(T.tile_words));
+        const int blocks = (int)std::min<int64_t>(n_items, (int64_t)device_sm_count() * 2);
+        note_launch();
+        k_delta_tile<<<blocks, kDeltaTileThreads, (size_t)T.tile_words * 4, st>>>(A);
         BBC_CUDA_TRY(cudaGetLastError());
         unsigned long long h[2] = {0, 0};
         BBC_CUDA_TRY(cudaMemcpyAsync(h, out, 16, cudaMemcpyDeviceToHost, st));
