@@ -147,8 +147,9 @@ def test_what_the_learned_model_gains_over_the_wedge_estimate(gpu_lib):
     compared with the best affine map of the wedge share (least squares on the same
     training items). Ordering the queue by either gives the same makespan here (the
     wedge share already ranks items almost perfectly, and even the true costs leave
-    under 1 % to gain), which the test reports and bounds. The paper's own order, by
-    each anchor's fanout (Algorithm 4), is simulated beside them."""
+    under 1 % to gain): the network gains nothing for the schedule, which the test
+    reports and bounds in both directions. The paper's own order, by each anchor's
+    fanout (Algorithm 4), is simulated beside them."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     Xs, cs = [], []
     for seed, scale in ((21, 0.05), (22, 0.08), (23, 0.12), (24, 0.15)):
@@ -191,10 +192,16 @@ def test_what_the_learned_model_gains_over_the_wedge_estimate(gpu_lib):
               f"rank correlation: network {rho_model:.3f}, wedge share {rho_share:.3f}; "
               f"simulated makespan (cycles): fanout order {ms_fanout:.4g}, wedge order {ms_share:.4g}, "
               f"learned {ms_model:.4g}, true-cost order {ms_best:.4g}")
+        # what the network gains: a better cost prediction ...
         assert mse_model < mse_share
         assert rho_model > rho_share - 0.02
-        assert ms_model <= 1.02 * ms_share
-        assert ms_model <= 1.02 * ms_fanout
+        # ... and no scheduling gain: the learned order's makespan is the wedge order's
+        # (and the fanout order's) to within 2 %, either way. Real tile-kernel times with
+        # the learned order against the default order showed no gain either (measured,
+        # not asserted here: 18.31 against 18.34 ms on the 20M-edge graph, 28.2-29.0
+        # against 28.3 ms on the 100M-edge heavy-hub graph).
+        assert abs(ms_model - ms_share) <= 0.02 * ms_share
+        assert abs(ms_model - ms_fanout) <= 0.02 * ms_fanout
         # the real queue with the learned order: same counts
         before = G.count()[:2]
         m.order(G)
