@@ -466,6 +466,22 @@ def bench_serving(args, pool):
     large = synth.large_serving_graph(seed=0)
     lg = read_golden("serve_large_200k_100k_5m")
     large_want = int(lg["balanced"]) if lg is not None else None
+    # one large request alone: its reservation against the device memory it reached (the
+    # library pool's high-water mark, preparation temporaries and tick buffers included)
+    srv = bbc.Server(8 << 30)
+    warm = srv.submit(gs[0])
+    srv.wait(warm, timeout_s=60.0)
+    used0, _ = bbc.memory_usage(reset_high=True)
+    t = srv.submit(large)
+    got_large = srv.wait(t, timeout_s=600.0)
+    _, high = bbc.memory_usage()
+    q = srv.request_info(t)
+    srv.close()
+    alone = {"wedges": q["wedges"], "reserved_gb": q["reserved_bytes"] / 1e9,
+             "measured_peak_gb": (high - used0) / 1e9, "latency_ms": q["latency_us"] / 1e3,
+             "prepare_ms": q["prepare_us"] / 1e3, "count_ms": q["count_us"] / 1e3,
+             "ticks": q["ticks"], "tick_gpu_ms": q["tick_gpu_us"] / 1e3,
+             "exact": got_large == large_want if large_want is not None else None}
     rng = np.random.default_rng(0)
     out = []
     for rate in args.serve_rates:
@@ -517,7 +533,7 @@ def bench_serving(args, pool):
         })
     return {"budget_gb": 8, "latency": "submit to completion, library clock",
             "exact_against": "tests/golden (CPU oracle): batch members and the 5M-edge request",
-            "rates": out}
+            "large_request_alone": alone, "rates": out}
 
 
 GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")

@@ -31,7 +31,10 @@ namespace bbc {
 namespace {
 
 using Clock = std::chrono::steady_clock;
-constexpr int kPrepThreads = 6;     // preparation threads per server
+// Preparation threads per server. Preparing a small request is mostly kernel launches
+// and stream synchronisations, which contend in the driver: 16 threads prepared fewer
+// requests per second than 6 (2,390 against 2,720 at saturation).
+constexpr int kPrepThreads = 6;
 
 struct Request {
     uint64_t ticket = 0;
