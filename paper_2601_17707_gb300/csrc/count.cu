@@ -478,25 +478,26 @@ struct WarpStage {
 // One warp's pass over all oriented wedges of anchor rows [sb, se) (the warp kernels'
 // sweep: their anchors fit one counter table). MODE 0 bumps the counters; MODE 1 (the
 // per-vertex centre pass) reads them and adds (count - 1) per wedge to the centre's b.
-// Warps take batches of 32 centres from *batch_ctr; lane j owns centre j's slice. Long
+// Warps take batches of `batch` (<= 32) centres from *batch_ctr; lane j owns centre j's
+// slice. Long
 // slices are swept by the whole warp with 16-byte loads; short ones are compacted into
 // the warp's stage and walked lane-interleaved (walk_short). Per-centre sums of a batch
 // stay below 2^32: a slice's counts add up to at most the number of edges.
 template <int MODE, class Counter>
 __device__ __forceinline__ void warp_sweep(const DevGraph &G, int64_t sb, int64_t se,
                                       const Counter &ctr, int *batch_ctr, uint32_t *sacc,
-                                      WarpStage &ws) {
+                                      WarpStage &ws, int batch = 32) {
     const int lane = threadIdx.x & 31;
-    const int64_t nbatch = (se - sb + 31) >> 5;
+    const int64_t nbatch = (se - sb + batch - 1) / batch;
     const uint32_t *__restrict__ rowC = G.rowC;
     for (;;) {
         int bi = 0;
         if (lane == 0) bi = atomicAdd(batch_ctr, 1);
         bi = __shfl_sync(kFull, bi, 0);
         if (bi >= nbatch) break;
-        const int64_t ci = sb + (int64_t)bi * 32 + lane;
+        const int64_t ci = sb + (int64_t)bi * batch + lane;
         uint32_t b = 0, len = 0, sg = 0, c = 0;
-        if (ci < se) {
+        if (lane < batch && ci < se) {
             // the whole endpoint range of the anchor inside row c (known from preparation)
             const uint32_t ent = __ldg(G.rowS + ci);
             c = ent & kIdMask;
@@ -1124,12 +1125,16 @@ __device__ void group_tile_item(const DevGraph &G, int a, uint32_t *tile, int gr
     const uint32_t lo = BlockTile<CW>::origin(lo0);   // the table's first endpoint slot
     if (gt == 0) *batch_ctr = 0;
     group_sync<GW>(grp);
-    warp_sweep<0>(G, sb, se, ctr, batch_ctr, nullptr, ws);
+    // a group shares an anchor's centres in batches small enough for every warp to get
+    // some: an anchor of few centres with long rows would otherwise keep one warp busy
+    const int64_t per_warp = (se - sb + GW - 1) / GW;
+    const int batch = GW == 1 ? 32 : (per_warp < 4 ? 4 : (per_warp > 32 ? 32 : (int)per_warp));
+    warp_sweep<0>(G, sb, se, ctr, batch_ctr, nullptr, ws, batch);
     group_sync<GW>(grp);
     if (G.bC) {
         if (gt == 0) *batch_ctr = 0;
         group_sync<GW>(grp);
-        warp_sweep<1>(G, sb, se, ctr, batch_ctr, sacc, ws);
+        warp_sweep<1>(G, sb, se, ctr, batch_ctr, sacc, ws, batch);
         group_sync<GW>(grp);
     }
     const uint32_t n = hi - lo;
