@@ -80,7 +80,9 @@ typedef struct bbc_tuning {
     int32_t queue_chunk;       /* work items a warp (or warp group) of the light-anchor
                                   kernels takes from its queue per atomic access (1..64;
                                   0: the default, 1) */
-    int32_t reserved;
+    int32_t group_warps;       /* warps sharing one counter table in the group-tile kernel:
+                                  4 (0: the default) or 8 (a table of twice the endpoints,
+                                  so wider single-tile anchors leave the block-tile kernel) */
 } bbc_tuning;
 
 /* Fills *t with the built-in defaults. */
@@ -232,9 +234,10 @@ bbc_status bbc_count_batch(int32_t n, bbc_graph *const *gs, uint64_t *balanced,
 
 /*
  * bbc_autotune_batch -- times bbc_count_batch on these graphs while searching, one knob
- * at a time from the defaults, the counter-tile size (tile_words), the light-anchor
- * threshold (warp_max_wedges), the heavy-anchor split size (split_wedges), the resident
- * blocks per SM and the queue chunk (queue_chunk), and stores the fastest choice in *best.
+ * at a time from the defaults, the group-tile width (group_warps), the counter-tile size
+ * (tile_words), the light-anchor threshold (warp_max_wedges), the heavy-anchor split size
+ * (split_wedges), the resident blocks per SM and the queue chunk (queue_chunk), and stores
+ * the fastest choice in *best.
  * The choice is also kept for NULL-tuning batch calls on batches of the same shape bucket
  * (the SM count, the number of graphs and the binary orders of magnitude of their edges,
  * wedges and pair-side vertices), in the process and in a cache file that later processes

@@ -95,11 +95,11 @@ class Tuning(ctypes.Structure):
         ("blocks_per_sm", ctypes.c_int32),
         ("plain", ctypes.c_int32),
         ("queue_chunk", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("group_warps", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _LIB = None

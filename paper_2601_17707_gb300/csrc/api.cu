@@ -208,7 +208,9 @@ Tuning resolve_tuning(const bbc_tuning *t, int sm_count) {
     r.blocks_per_sm = 2;
     r.plain = 0;
     r.queue_chunk = 1;
+    r.group_warps = kGroupWarps;
     if (t) {
+        if (t->group_warps == 8) r.group_warps = 8;
         if (t->queue_chunk > 0) r.queue_chunk = t->queue_chunk < 64 ? t->queue_chunk : 64;
         r.plain = t->plain ? 1 : 0;
         if (t->blocks_per_sm == 1 || t->blocks_per_sm == 2) r.blocks_per_sm = t->blocks_per_sm;
@@ -336,6 +338,7 @@ bbc_status bbc_tuning_default(bbc_tuning *t) {
     t->blocks_per_sm = r.blocks_per_sm;
     t->plain = 0;
     t->queue_chunk = r.queue_chunk;
+    t->group_warps = r.group_warps;
     return BBC_OK;
 }
 

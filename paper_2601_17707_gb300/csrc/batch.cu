@@ -84,7 +84,7 @@ std::map<std::vector<long long>, Tuning> g_tuned;
 bool g_tune_loaded = false;
 
 // The persisted tuning cache: one line per shape key, "key... : tile_words warp_max_wedges
-// split_wedges blocks_per_sm queue_chunk". Its path is $BBC_TUNE_CACHE, else
+// split_wedges blocks_per_sm queue_chunk group_warps". Its path is $BBC_TUNE_CACHE, else
 // $XDG_CACHE_HOME/bbc/batch_tuning.txt, else $HOME/.cache/bbc/batch_tuning.txt; an empty
 // BBC_TUNE_CACHE turns persistence off.
 std::string tune_cache_path() {
@@ -114,9 +114,9 @@ void load_tune_cache_locked() {
             key.push_back(v);
             p = end;
         }
-        long long tw = 0, wm = 0, sp = 0, bp = 0, qc = 0;
+        long long tw = 0, wm = 0, sp = 0, bp = 0, qc = 0, gw = 0;
         if (key.size() != 5 ||
-            sscanf(colon + 1, "%lld %lld %lld %lld %lld", &tw, &wm, &sp, &bp, &qc) != 5)
+            sscanf(colon + 1, "%lld %lld %lld %lld %lld %lld", &tw, &wm, &sp, &bp, &qc, &gw) != 6)
             continue;
         bbc_tuning t{};
         t.tile_words = (int32_t)tw;
@@ -124,6 +124,7 @@ void load_tune_cache_locked() {
         t.split_wedges = (int32_t)std::min<long long>(sp, INT32_MAX);
         t.blocks_per_sm = (int32_t)bp;
         t.queue_chunk = (int32_t)qc;
+        t.group_warps = (int32_t)gw;
         g_tuned[key] = resolve_tuning(&t, device_sm_count());
     }
     fclose(f);
@@ -146,8 +147,8 @@ void save_tune_cache_locked() {
     for (const auto &kv : g_tuned) {
         for (long long v : kv.first) fprintf(f, "%lld ", v);
         const Tuning &t = kv.second;
-        fprintf(f, ": %d %d %lld %d %d\n", t.tile_words, t.warp_max_wedges, t.split_wedges,
-                t.blocks_per_sm, t.queue_chunk);
+        fprintf(f, ": %d %d %lld %d %d %d\n", t.tile_words, t.warp_max_wedges, t.split_wedges,
+                t.blocks_per_sm, t.queue_chunk, t.group_warps);
     }
     const bool ok = fclose(f) == 0;
     if (ok) rename(tmp.c_str(), path.c_str());
@@ -176,7 +177,7 @@ std::vector<long long> shape_key(int32_t n, bbc_graph *const *gs) {
 bool same_tuning(const Tuning &a, const Tuning &b) {
     return a.tile_words == b.tile_words && a.warp_max_wedges == b.warp_max_wedges &&
            a.split_wedges == b.split_wedges && a.blocks_per_sm == b.blocks_per_sm &&
-           a.plain == b.plain && a.queue_chunk == b.queue_chunk;
+           a.plain == b.plain && a.queue_chunk == b.queue_chunk && a.group_warps == b.group_warps;
 }
 
 #define BBC_LAUNCH_OK(what)                                        \
@@ -502,12 +503,14 @@ bbc_status bbc_autotune_batch(int32_t n, bbc_graph *const *gs, bbc_tuning *best,
         best_t.blocks_per_sm = 2;
         best_t.warp_max_wedges = 256;
         best_t.queue_chunk = 1;
+        best_t.group_warps = 4;
         float best_ms = 1e30f;
         BBC_TRY(timed(best_t, &best_ms));
         const std::vector<int> knob_tiles = {0, 16384, 8192, 4096};
         const std::vector<int> knob_warp = {64, 256, 512};
         const std::vector<int> knob_blocks = {1, 2};
         const std::vector<int> knob_chunk = {1, 4, 16};
+        const std::vector<int> knob_group = {4, 8};
         const std::vector<long long> knob_split = {s_auto / 4, s_auto, 4 * s_auto};
         auto sweep = [&](auto values, auto set) -> bbc_status {
             bbc_tuning keep = best_t;
@@ -524,6 +527,7 @@ bbc_status bbc_autotune_batch(int32_t n, bbc_graph *const *gs, bbc_tuning *best,
             }
             return BBC_OK;
         };
+        BBC_TRY(sweep(knob_group, [](bbc_tuning &t, int v) { t.group_warps = v; }));
         BBC_TRY(sweep(knob_tiles, [](bbc_tuning &t, int v) { t.tile_words = v; }));
         BBC_TRY(sweep(knob_warp, [](bbc_tuning &t, int v) { t.warp_max_wedges = v; }));
         BBC_TRY(sweep(knob_split, [](bbc_tuning &t, long long v) {
@@ -558,6 +562,7 @@ bbc_status bbc_batch_tuning(int32_t n, bbc_graph *const *gs, bbc_tuning *out) {
         out->blocks_per_sm = T.blocks_per_sm;
         out->plain = T.plain;
         out->queue_chunk = T.queue_chunk;
+        out->group_warps = T.group_warps;
         return BBC_OK;
     } catch (...) {
         set_error("unexpected exception in bbc_batch_tuning");

@@ -138,6 +138,7 @@ struct Tuning {
     int plain;                 // static one-block-per-anchor schedule (Algorithm 3)
     int tiles_only = 0;        // every anchor on block tiles (no hash or warp/group tiles)
     int queue_chunk = 1;       // items per queue access of the warp and group kernels
+    int group_warps = 4;       // warps per table of the group-tile kernel (4 or 8)
 };
 
 Tuning resolve_tuning(const bbc_tuning *t, int sm_count);

@@ -1403,6 +1403,9 @@ bbc_status configure_count_kernels() {
         BBC_CUDA_TRY(cudaFuncSetAttribute(k_group_tile<kGroupWarps>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           kWtWarps * kWtWords * 4));
+        BBC_CUDA_TRY(cudaFuncSetAttribute(k_group_tile<2 * kGroupWarps>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          kWtWarps * kWtWords * 4));
         configured_device = dev;
     }
     return BBC_OK;
@@ -1508,9 +1511,9 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
         cudaStream_t st = begin_side();
         const int tok = profile_begin(kProfGroupTile, st);
         note_launch();
-        constexpr int groups = kWtWarps / kGroupWarps;
-        k_group_tile<kGroupWarps><<<std::min((L.n_gt_items + groups - 1) / groups, sms * 2), kWtThreads,
-                                    kWtWarps * kWtWords * 4, st>>>(
+        const int groups = kWtWarps / T.group_warps;
+        auto kern = T.group_warps == 2 * kGroupWarps ? k_group_tile<2 * kGroupWarps> : k_group_tile<kGroupWarps>;
+        kern<<<std::min((L.n_gt_items + groups - 1) / groups, sms * 2), kWtThreads, kWtWarps * kWtWords * 4, st>>>(
             L.graphs, L.gt_items, L.n_gt_items, &L.queue->gt_head, T.queue_chunk);
         BBC_CUDA_TRY(cudaGetLastError());
         profile_end(tok, st);

@@ -238,6 +238,7 @@ struct ClassifyParams {
     long long split;
     int warp_tiles;            // single-tile anchors that fit a warp's table go to k_warp_tile
     int var_width;             // block tiles choose their counter width tile by tile
+    int group_warps;           // warps per group-tile table (its capacity)
 };
 
 // Work of one anchor: kind 0 none, 1 warp-hash item, 2 tile items, 3 warp-tile item (its
@@ -271,7 +272,7 @@ __device__ __forceinline__ void classify_one(const ClassifyParams &P, const int6
         *groups = 1;
         return;
     }
-    if (P.warp_tiles && span + slack <= (long long)group_tile_endpoints(kGroupWarps, w)) {
+    if (P.warp_tiles && span + slack <= (long long)group_tile_endpoints(P.group_warps, w)) {
         *kind = 4;
         *cw = w;
         *ntiles = 1;
@@ -496,7 +497,7 @@ bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
     if (g->items_valid && g->items_tuning.tile_words == t.tile_words &&
         g->items_tuning.warp_max_wedges == t.warp_max_wedges &&
         g->items_tuning.split_wedges == t.split_wedges && g->items_tuning.plain == t.plain &&
-        g->items_tuning.tiles_only == t.tiles_only)
+        g->items_tuning.tiles_only == t.tiles_only && g->items_tuning.group_warps == t.group_warps)
         return BBC_OK;
     if (g->tile_items) dev_free(g->tile_items, st);
     if (g->warp_items) dev_free(g->warp_items, st);
@@ -535,7 +536,7 @@ bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
     BBC_TRY(sc.get(&nb, (size_t)nS));
     BBC_TRY(dev_alloc_n(&g->boff, (size_t)nS + 1, st));
     ClassifyParams P{g->nS, g->orient_low, t.tile_words, t.warp_max_wedges, t.split_wedges,
-                     (t.plain || t.tiles_only) ? 0 : 1, t.tiles_only ? 0 : 1};
+                     (t.plain || t.tiles_only) ? 0 : 1, t.tiles_only ? 0 : 1, t.group_warps};
     note_launch();
     k_classify<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, nt, nh, nb, nw, ng);
     BBC_LAUNCH_CHECK("k_classify");

@@ -53,7 +53,8 @@ def test_batch_tunings_and_autotune_agree(gpu_lib, batch_graphs):
     try:
         for kw in (dict(tile_words=1024, warp_max_wedges=1), dict(warp_max_wedges=512),
                    dict(blocks_per_sm=1), dict(tile_words=4096, split_wedges=200),
-                   dict(queue_chunk=1), dict(queue_chunk=64, warp_max_wedges=512)):
+                   dict(queue_chunk=1), dict(queue_chunk=64, warp_max_wedges=512),
+                   dict(group_warps=8), dict(group_warps=8, blocks_per_sm=1)):
             t = bbc.default_tuning()
             for k, v in kw.items():
                 setattr(t, k, v)
@@ -256,7 +257,7 @@ def test_autotune_choice_persists_across_processes(gpu_lib, tmp_path):
     first = run(True)
     assert (tmp_path / "tune.txt").exists()
     second = run(False)
-    keys = ("tile_words", "warp_max_wedges", "blocks_per_sm", "queue_chunk")
+    keys = ("tile_words", "warp_max_wedges", "blocks_per_sm", "queue_chunk", "group_warps")
     # the first process serves its own batches with the choice it found ...
     for k in keys:
         assert first["best"][k] in (0, first["used"][k]), k

@@ -82,7 +82,8 @@ def test_random_graphs_all_paths(gpu_lib, seed):
     # splits, one block per SM, both orientations and both pair sides
     for t in (None, tuning(warp_max_wedges=1), tuning(warp_max_wedges=512),
               tuning(tile_words=1024, split_wedges=64), tuning(blocks_per_sm=1, tile_words=53248),
-              tuning(plain=1), tuning(plain=1, tile_words=1024)):
+              tuning(plain=1), tuning(plain=1, tile_words=1024), tuning(group_warps=8),
+              tuning(group_warps=8, queue_chunk=7)):
         assert_parity(g, tuning=t, want=want)
     for flags in (bbc.ORIENT_LOW_ANCHOR, bbc.SIDE_FORCE_U, bbc.SIDE_FORCE_V,
                   bbc.SIDE_FORCE_V | bbc.ORIENT_LOW_ANCHOR):
