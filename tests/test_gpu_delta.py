@@ -76,6 +76,50 @@ def test_powerlaw_batches_at_hubs(gpu_lib):
     _check(g, *_batch(rng, g, 400), device=True)
 
 
+def _wide_graph():
+    """60,000 pair-side (U) vertices over 70,000 centres, so that an anchor's endpoint range
+    spans several counter tiles: vertex 0 on every centre and vertex 1 on 66,000 of them
+    (counts past 65,535: 32-bit counters), 100 vertices on 300 centres each (16-bit), the
+    rest on three centres each (8-bit)."""
+    rng = np.random.default_rng(8)
+    n_u, n_v = 60_000, 70_000
+    us = [np.zeros(n_v, np.int64), np.ones(66_000, np.int64)]
+    vs = [np.arange(n_v), np.arange(66_000)]
+    mid = rng.choice(np.arange(2, n_u), size=100, replace=False)
+    for x in mid:
+        us.append(np.full(300, x))
+        vs.append(rng.choice(n_v, size=300, replace=False))
+    rest = np.setdiff1d(np.arange(2, n_u), mid)
+    us.append(np.repeat(rest, 3))
+    vs.append(rng.integers(0, n_v, size=3 * rest.size))
+    key = np.unique(np.concatenate(us) * n_v + np.concatenate(vs))
+    u = (key // n_v).astype(np.int32)
+    v = (key % n_v).astype(np.int32)
+    sign = np.where(rng.random(key.size) < 0.6, 1, -1).astype(np.int8)
+    return synth.SignedBipartite(n_u, n_v, u, v, sign), mid
+
+
+def test_wide_anchors_over_several_tiles_and_counter_widths(gpu_lib):
+    """Updates at the two hubs (32-bit counters), at 300-centre vertices (16-bit) and at
+    light ones (8-bit), on a pair side wider than one counter tile."""
+    g, mid = _wide_graph()
+    rng = np.random.default_rng(9)
+    present = {(a, b): s for a, b, s in zip(g.u.tolist(), g.v.tolist(), g.sign.tolist())}
+    picks = [(0, 5), (0, 69_999), (1, 10), (1, 67_000)] + [(int(x), int(rng.integers(0, g.n_v))) for x in mid[:20]]
+    picks += [(int(a), int(rng.integers(0, g.n_v))) for a in rng.integers(2, g.n_u, size=30)]
+    out, seen = [], set()
+    for a, b in picks:
+        if (a, b) in seen:
+            continue
+        seen.add((a, b))
+        if (a, b) in present:
+            out.append((a, b, int(rng.choice([0, -present[(a, b)]]))))
+        else:
+            out.append((a, b, int(rng.choice([1, -1]))))
+    u, v, s = (np.array(x, dt) for x, dt in zip(zip(*out), (np.int32, np.int32, np.int8)))
+    _check(g, u, v, s, flags=bbc.SIDE_FORCE_U)
+
+
 def test_switching_a_vertex_changes_nothing(gpu_lib):
     g = synth.uniform_graph(200, 100, 4_000, 0.5, seed=5)
     x = int(np.bincount(g.u).argmax())
