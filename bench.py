@@ -104,16 +104,17 @@ def code_only(text: str) -> str:
 
 def kernel_source_digest() -> str:
     h = hashlib.sha256()
-    for name in ("count.cu", "bbc_internal.cuh", "graph.cuh"):
+    for name in ("count.cu", "prep.cu", "bbc_internal.cuh", "graph.cuh"):
         with open(os.path.join(ROOT, "paper_2601_17707_gb300", "csrc", name), encoding="utf-8") as f:
             h.update(code_only(f.read()).encode())
     return h.hexdigest()
 
 
 def recorded_traffic(workload: str = WORKLOAD):
-    """Per-launch DRAM bytes of the tile kernel from the committed ncu summary of this
-    workload (profiles/k_tile_<workload>.traffic.json), or None when there is none or the
-    kernel source changed since that capture."""
+    """Per-step DRAM bytes of the tile path (the k_tile launch, plus the k_tile_cs launch
+    of graphs with centre-split tiles) from the committed ncu summary of this workload
+    (profiles/k_tile_<workload>.traffic.json), or None when there is none or the kernel
+    source changed since that capture."""
     try:
         with open(os.path.join(TRAFFIC_DIR, f"k_tile_{workload}.traffic.json")) as f:
             rec = json.load(f)
@@ -701,15 +702,22 @@ def single_graph(args, workload, steps, warmup, dev, dist, world, with_e2e):
     peak, peak_kind = hbm_peak()
     roof = None
     tile_launches, tile_ms = prof.get("k_tile", (0, 0.0))
+    # graphs with centre-split tiles finish their centre pass in a second launch per step
+    # (k_tile_cs): the tile path is both
+    cs_launches, cs_ms = prof.get("k_tile_cs", (0, 0.0))
     if tile_launches:
         alg_bytes = 4 * 2 * W + 20 * g.n_edges   # per launch (one launch per step)
-        achieved = alg_bytes / (tile_ms / tile_launches / 1e3) / 1e9
+        path_ms = (tile_ms + cs_ms) / tile_launches
+        achieved = alg_bytes / (path_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": recorded_traffic(workload),
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-                else "fallback 6.8 TB/s", "kernel": "k_tile",
-                "kernel_ms_per_launch": tile_ms / tile_launches,
+                else "fallback 6.8 TB/s", "kernel": "k_tile + k_tile_cs" if cs_launches else "k_tile",
+                "kernel_ms_per_launch": path_ms,
                 "algorithmic_bytes_per_launch": alg_bytes}
+        if cs_launches:
+            roof["k_tile_ms_per_launch"] = tile_ms / tile_launches
+            roof["k_tile_cs_ms_per_launch"] = cs_ms / cs_launches
     co = None
     n_co, ms_co = prof_co.get("k_tile", (0, 0.0))
     if n_co:

@@ -72,7 +72,12 @@ typedef struct bbc_tuning {
                                   one-warp hash path (<= 512) */
     int32_t dense_min_permille;/* reserved for a block-level hash path (unused) */
     int32_t split_wedges;      /* anchors with more wedges than this are split into
-                                  tile-range items that run on different blocks */
+                                  tile-range items that run on different blocks; an
+                                  anchor heavier than split_wedges times its tiles also
+                                  has each tile's centres cut into parts (up to 64, of
+                                  about split_wedges / 8 wedges) whose counts are merged
+                                  in device memory (at most the larger of 8 bytes per
+                                  edge and 16 MiB, else no centre split) */
     int32_t blocks_per_sm;     /* resident blocks per SM of the tile kernel (1 or 2) */
     int32_t plain;             /* 1: the static schedule of G-BBC (Algorithm 3) -- one block
                                   per anchor in rank order, no work queue, no heavy-first

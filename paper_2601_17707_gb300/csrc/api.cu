@@ -58,13 +58,20 @@ __global__ void k_scatter_per_vertex(const unsigned long long *__restrict__ by_r
 }  // namespace
 
 // Wedges and pair-side edges of the anchors behind a work list (one entry per anchor:
-// a tile anchor's first item, or its single hash / warp-tile / group-tile item).
+// a tile anchor's first item (tile 0, part 0 when centre-split), or its single hash /
+// warp-tile / group-tile item).
 __global__ void k_work_tile(const TileItem *__restrict__ items, int n, const int64_t *__restrict__ rowS_off,
-                            const unsigned long long *__restrict__ wl, unsigned long long *__restrict__ out) {
+                            const unsigned long long *__restrict__ wl, const CentreSplit *__restrict__ cs_desc,
+                            unsigned long long *__restrict__ out) {
     unsigned long long w = 0, e = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const TileItem it = items[i];
-        if (it.tile_begin != 0) continue;
+        if (is_centre_split(it)) {
+            const CentreSplit d = cs_desc[it.tile_begin];
+            if (d.tile != 0 || d.part != 0) continue;
+        } else if (it.tile_begin != 0) {
+            continue;
+        }
         w += wl[it.anchor];
         e += (unsigned long long)(rowS_off[it.anchor + 1] - rowS_off[it.anchor]);
     }
@@ -118,7 +125,7 @@ struct ProfSlot {
 };
 std::vector<ProfSlot> g_prof;
 const char *const kProfNames[kProfKinds] = {"k_tile", "k_warp_hash", "k_warp_tile", "k_group_tile",
-                                            "k_tile_motif"};
+                                            "k_tile_motif", "k_tile_cs"};
 }  // namespace
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -260,6 +267,7 @@ bbc_status count_graph(bbc_graph *g, uint64_t *totals_dev, uint64_t *per_u, uint
     }
     BBC_CUDA_TRY(cudaMemsetAsync(g->totals, 0, 16, st));
     BBC_CUDA_TRY(cudaMemsetAsync(g->queue, 0, sizeof(QueueState), st));
+    BBC_TRY(clear_centre_split(g, st));
     static_assert(sizeof(DevGraph) % 8 == 0, "descriptor layout");
     DevGraph d = host_descriptor(g, pv, true);
     note_launch();
@@ -278,6 +286,10 @@ bbc_status count_graph(bbc_graph *g, uint64_t *totals_dev, uint64_t *per_u, uint
     L.queue = g->queue;
     L.tuning = T;
     L.prefetch = rows_exceed_l2(g);
+    if (pv) {
+        L.cs_items = g->cs_items;
+        L.n_cs_items = g->n_cs_items;
+    }
     BBC_TRY(launch_count(L, st));
     if (pv) {
         uint64_t *outS = g->side == 0 ? per_u : per_v;
@@ -504,7 +516,7 @@ bbc_status bbc_graph_work(bbc_graph *g, uint64_t *out, void *cuda_stream) {
         if (e == cudaSuccess && g->n_tile > 0) {
             note_launch();
             k_work_tile<<<std::min((g->n_tile + 255) / 256, 1024), 256, 0, st>>>(g->tile_items, g->n_tile,
-                                                                                  g->rowS_off, g->wl, d);
+                                                                                  g->rowS_off, g->wl, g->cs_desc, d);
         }
         const HashItem *lists[3] = {g->gt_items, g->wt_items, g->warp_items};
         for (int k = 0; k < 3 && e == cudaSuccess; ++k)

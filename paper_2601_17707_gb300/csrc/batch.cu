@@ -58,6 +58,7 @@ struct Plan {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t exec = nullptr;
     CountLaunch launch{};                     // what the graph records (for profiled runs)
+    std::vector<const bbc_graph *> cs_graphs; // members with centre-split tiles (cleared per run)
 
     ~Plan() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -296,12 +297,17 @@ bbc_status build_plan(int32_t n, bbc_graph *const *gs, const Tuning &T, std::uni
     L.tuning = T;
     for (int i = 0; i < n; ++i) L.prefetch = L.prefetch || rows_exceed_l2(gs[i]);
     P->launch = L;
+    for (int i = 0; i < n; ++i)
+        if (gs[i]->n_cs_groups > 0) P->cs_graphs.push_back(gs[i]);
     BBC_TRY(configure_count_kernels());
     BBC_TRY(ensure_side_streams());   // no stream or event creation inside the capture
     BBC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     cudaMemsetAsync(P->totals, 0, sizeof(unsigned long long) * 2 * (size_t)n, st);
     cudaMemsetAsync(P->queue, 0, sizeof(QueueState), st);
-    bbc_status ls = launch_count(L, st);
+    bbc_status ls = BBC_OK;
+    for (const bbc_graph *cg : P->cs_graphs)
+        if (ls == BBC_OK) ls = clear_centre_split(cg, st);
+    if (ls == BBC_OK) ls = launch_count(L, st);
     cudaMemcpyAsync(P->host_totals, P->totals, sizeof(unsigned long long) * 2 * (size_t)n,
                     cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(host_error_word(P.get()), &P->queue->error, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
@@ -365,6 +371,7 @@ bbc_status run_plan(Plan *p, uint64_t *balanced, cudaStream_t st, float *ms) {
         BBC_CUDA_TRY(cudaMemsetAsync(p->totals, 0, sizeof(unsigned long long) * 2 * (size_t)p->n,
                                      p->stream));
         BBC_CUDA_TRY(cudaMemsetAsync(p->queue, 0, sizeof(QueueState), p->stream));
+        for (const bbc_graph *cg : p->cs_graphs) BBC_TRY(clear_centre_split(cg, p->stream));
         BBC_TRY(launch_count(p->launch, p->stream));
         BBC_CUDA_TRY(cudaMemcpyAsync(p->host_totals, p->totals,
                                      sizeof(unsigned long long) * 2 * (size_t)p->n,

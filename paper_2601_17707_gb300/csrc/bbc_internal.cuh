@@ -15,6 +15,8 @@ namespace bbc {
 constexpr uint32_t kSignBit = 0x80000000u;
 constexpr uint32_t kIdMask = 0x7fffffffu;
 
+struct CentreSplit;
+
 // One prepared graph as the counting kernels see it. S is the pair (anchor/endpoint)
 // side, C the centre side; both are relabelled by rank (degree descending, id
 // descending, Def. 6). Entries pack the neighbour's rank with the edge sign in bit 31
@@ -38,12 +40,21 @@ struct DevGraph {
                                // boundary t (1 <= t < tiles) of entry i of anchor a is
                                // bnd[boff[a] + (t - 1) * degree(a) + i], an index into rowC
     const int64_t *boff;
+    // centre-split tiles (items with parts): per tile group, the merged counters
+    // (cs_group_words words: p, n of endpoint lo + i at 2 i, 2 i + 1) and an arrival
+    // counter; both zeroed before every count launch
+    const CentreSplit *cs_desc;
+    uint32_t *cs_buf;
+    unsigned *cs_arrive;
+    int64_t cs_group_words;
 };
 
 // A unit of work of the tile kernel: anchor `anchor` of graph `graph`, endpoint tiles
 // [tile_begin, tile_end) over the anchor's endpoint range. The top two bits of
 // `tile_end_cw` hold the counter width code (0: 8-bit, 1: 16-bit, 2: 32-bit counters),
-// which fixes the endpoints per tile (2, 1 or 1/2 per shared-memory word).
+// which fixes the endpoints per tile (2, 1 or 1/2 per shared-memory word). Bit 29 marks
+// a centre-split item: it covers one tile and one part of the anchor's centres, and
+// `tile_begin` indexes its CentreSplit record (DevGraph::cs_desc) instead.
 struct TileItem {
     int32_t graph;
     int32_t anchor;
@@ -51,8 +62,21 @@ struct TileItem {
     uint32_t tile_end_cw;
 };
 
-__host__ __device__ inline int tile_end_of(const TileItem &t) { return (int)(t.tile_end_cw & 0x3fffffffu); }
+constexpr uint32_t kCentreSplitBit = 1u << 29;
+__host__ __device__ inline int tile_end_of(const TileItem &t) { return (int)(t.tile_end_cw & 0x1fffffffu); }
 __host__ __device__ inline int tile_width_of(const TileItem &t) { return (int)(t.tile_end_cw >> 30); }
+__host__ __device__ inline bool is_centre_split(const TileItem &t) { return (t.tile_end_cw & kCentreSplitBit) != 0; }
+
+// One part of a centre-split tile: tile `tile` of the anchor, centres [part / parts,
+// (part + 1) / parts) of its S -> C row (by position), merged through tile group `group`.
+struct CentreSplit {
+    int32_t tile;
+    int16_t part, parts;
+    int32_t group;
+    int32_t pad;
+};
+// Most parts of one centre-split tile.
+constexpr int kMaxParts = 64;
 
 // Counter widths of a block tile: 0 two 8-bit, 1 two 16-bit, 2 two 32-bit counters per
 // endpoint. A tile item whose width field is kWidthPerTile chooses the width tile by
@@ -118,7 +142,7 @@ __host__ __device__ constexpr uint32_t group_tile_endpoints(int gw, int cw) {
 struct QueueState {
     unsigned int tile_head;    // tile items
     unsigned int warp_head;    // hash items
-    unsigned int spare;
+    unsigned int cs_head;      // centre-split items (their centre pass)
     unsigned int error;        // nonzero: a kernel saw an impossible state (see kErr*)
     unsigned int wt_head;      // warp-tile items
     unsigned int gt_head;      // group-tile items
@@ -175,7 +199,10 @@ void note_launch();
 // Optional per-kernel timing (bbc_profile_start / bbc_profile_stop): while enabled, the
 // counting kernels are bracketed by CUDA events on their own stream. profile_begin
 // returns a token (-1 when profiling is off or the stream is being captured).
-enum { kProfTile = 0, kProfHash = 1, kProfWarpTile = 2, kProfGroupTile = 3, kProfMotif = 4, kProfKinds = 5 };
+enum {
+    kProfTile = 0, kProfHash = 1, kProfWarpTile = 2, kProfGroupTile = 3, kProfMotif = 4, kProfTileCs = 5,
+    kProfKinds = 6
+};
 int profile_begin(int kind, cudaStream_t st);
 bool profiling_active();
 void profile_end(int token, cudaStream_t st);
@@ -225,6 +252,10 @@ struct CountLaunch {
     long long *item_cycles = nullptr;  // device, per tile item: its duration in SM cycles
     bool prefetch = false;      // the graphs' C -> S rows are larger than L2: the tile kernel
                                 // asks for each slice's first lines ahead of use
+    // per-vertex counts only: the centre-split items again, for their centre pass after
+    // the tile kernel (the graphs' cs_buf and cs_arrive zeroed by the caller)
+    const TileItem *cs_items = nullptr;
+    int32_t n_cs_items = 0;
 };
 
 // One contiguous run of a graph's work items to copy into a combined list, tagged with

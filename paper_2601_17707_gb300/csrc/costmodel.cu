@@ -62,7 +62,8 @@ inline unsigned grid_blocks(int64_t n_warps_wanted) {
 //   0 log1p(anchor wedges) / 16      1 log1p(anchor degree) / 16
 //   2 log1p(tiles in the item) / 8   3 log1p(endpoint span of the item) / 16
 //   4 first tile / the anchor's tiles 5 counter width / 2
-//   6 log1p(|S|) / 16                7 log1p(wedges * item tiles / anchor tiles) / 16
+//   6 log1p(|S|) / 16                7 log1p(wedges * item tiles / anchor tiles
+//                                      [/ parts of a centre-split tile]) / 16
 __global__ void k_item_features(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items,
                                 int n, int tile_words, float *__restrict__ X) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -75,7 +76,15 @@ __global__ void k_item_features(const DevGraph *__restrict__ graphs, const TileI
         const double ept = cw == 0 ? 2.0 * tile_words : (cw == 1 ? (double)tile_words : tile_words / 2.0);
         const double range = G.orient_low ? (double)a : (double)(G.nS - 1 - a);
         const double nt = fmax(1.0, ceil(range / ept));
-        const int t0 = it.tile_begin, t1 = tile_end_of(it);
+        // a centre-split item: one tile, and a 1 / parts share of its centres
+        double share = 1.0;
+        int t0 = it.tile_begin, t1 = tile_end_of(it);
+        if (is_centre_split(it)) {
+            const CentreSplit d = G.cs_desc[it.tile_begin];
+            t0 = d.tile;
+            t1 = d.tile + 1;
+            share = 1.0 / d.parts;
+        }
         const double span = fmax(0.0, fmin(t1 * ept, range) - t0 * ept);
         float *x = X + (int64_t)i * kF;
         x[0] = (float)(log1p(wl) / 16.0);
@@ -85,7 +94,7 @@ __global__ void k_item_features(const DevGraph *__restrict__ graphs, const TileI
         x[4] = (float)(t0 / nt);
         x[5] = (float)(cw / 2.0);
         x[6] = (float)(log1p((double)G.nS) / 16.0);
-        x[7] = (float)(log1p(wl * (t1 - t0) / nt) / 16.0);
+        x[7] = (float)(log1p(wl * (t1 - t0) / nt * share) / 16.0);
     }
 }
 
@@ -558,6 +567,7 @@ bbc_status bbc_item_cycles(bbc_graph *g, int64_t *cycles_dev, int32_t capacity, 
         }
         BBC_CUDA_TRY(cudaMemsetAsync(g->totals, 0, 16, st));
         BBC_CUDA_TRY(cudaMemsetAsync(g->queue, 0, sizeof(QueueState), st));
+        BBC_TRY(clear_centre_split(g, st));
         if (g->n_tile > 0) BBC_CUDA_TRY(cudaMemsetAsync(cycles_dev, 0, (size_t)g->n_tile * 8, st));
         DevGraph d = host_descriptor(g, false, true);
         BBC_CUDA_TRY(cudaMemcpyAsync(g->dgraph, &d, sizeof d, cudaMemcpyHostToDevice, st));

@@ -607,6 +607,7 @@ struct SweepCtx {
     int t, nt;                    // this tile, and the anchor's number of tiles
     int64_t bbase;                // boff[anchor]
     int64_t deg;                  // the anchor's degree
+    int64_t row0;                 // the anchor's first S -> C entry
     bool single;                  // all centres fit one chunk: slices stay in shared memory
 };
 
@@ -670,7 +671,7 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
             uint32_t start = 0, len = 0;
             if (ci < se) {
                 ent = __ldg(G.rowS + ci);
-                find_slice(G, ci, ci - sb, X, start, len);
+                find_slice(G, ci, ci - X.row0, X, start, len);
             }
             // PF (graphs whose rows do not fit L2): each slice's first lines (all of a short
             // slice: at most 64 entries, three 128-byte lines) are requested now, so that
@@ -868,6 +869,7 @@ __device__ void run_tile_item(const DevGraph &G, const TileItem &item, int tile_
     X.nt = (int)((X.range_hi - X.range_lo + ept - 1) / ept);
     X.single = se - sb <= kChunk;
     X.deg = se - sb;
+    X.row0 = sb;
     X.bbase = G.boff ? G.boff[a] : 0;
     unsigned long long centre_carry = 0;   // single chunk: this thread's centre, all tiles
     for (int t = t0; t < t1; ++t) {
@@ -912,6 +914,7 @@ __device__ void run_tile_item_var(const DevGraph &G, const TileItem &item, int t
     X.nt = var_tile_count(G.rowS_off, bound, X.range_lo, X.range_hi, (uint32_t)tile_words);
     X.single = se - sb <= kChunk;
     X.deg = se - sb;
+    X.row0 = sb;
     X.bbase = G.boff ? G.boff[a] : 0;
     VarTile vt = var_tile_at(G.rowS_off, bound, X.range_lo, X.range_hi, (uint32_t)tile_words);
     for (int t = 0; t < t0; ++t) vt = var_tile_at(G.rowS_off, bound, vt.hi, X.range_hi, (uint32_t)tile_words);
@@ -930,6 +933,184 @@ __device__ void run_tile_item_var(const DevGraph &G, const TileItem &item, int t
     if (centre_carry) red_add(G.bC + (cs.ent[threadIdx.x] & kIdMask), centre_carry);
 }
 
+// ----------------------------------------------------------------------------- centre-split tiles
+//
+// An anchor with more wedges than its tiles can spread over the blocks (a hub with a
+// million centres and a handful of tiles would otherwise run alone for the whole launch)
+// has every tile cut into parts by centres. Part k of K sweeps the k-th K-th of the
+// anchor's S -> C row into its own shared tile, then adds the tile into the group's
+// merged counters in global memory (cs_buf, two 32-bit counters per endpoint). Counting
+// pairs needs the complete counts: without per-vertex output the part that arrives last
+// (cs_arrive) loads the merged counters back into its tile and runs the usual epilogue;
+// with per-vertex output a second launch (k_tile_cs) gives every part the merged tile for
+// its centre pass, and the last one of each group runs the epilogue.
+
+__device__ __forceinline__ void red_add_u32(uint32_t *p, uint32_t v) {
+    asm volatile("red.global.add.u32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(v) : "memory");
+}
+
+// Words of a tile whose endpoints run from origin org to hi (the epilogue's count).
+template <int CW>
+__device__ __forceinline__ uint32_t tile_words_of(uint32_t org, uint32_t hi) {
+    const uint32_t n = hi - org;
+    return CW == 0 ? (n + 1) / 2 : (CW == 1 ? n : 2 * n);
+}
+
+// Adds the tile of endpoints [lo, hi) (origin org) into merged counters buf (counter t of
+// endpoint w at 2 (w - lo) + t) and clears the tile. Counter c of the tile belongs to
+// endpoint org + c / 2 with type c & 1; with 8-bit counters an odd lo leaves the first
+// byte pair (endpoint lo - 1) at zero.
+template <int CW>
+__device__ void flush_tile(uint32_t *tile, uint32_t org, uint32_t lo, uint32_t hi, uint32_t *buf) {
+    const uint32_t words = tile_words_of<CW>(org, hi);
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) {
+        const uint32_t x = tile[i];
+        if (x == 0) continue;
+        tile[i] = 0;
+        if (CW == 0) {
+#pragma unroll
+            for (uint32_t b = 0; b < 4; ++b) {
+                const uint32_t v = (x >> (8 * b)) & 0xffu, w = org + 2 * i + (b >> 1);
+                if (v && w >= lo) red_add_u32(buf + 2 * (w - lo) + (b & 1), v);
+            }
+        } else if (CW == 1) {
+            if (x & 0xffffu) red_add_u32(buf + 2 * i, x & 0xffffu);
+            if (x >> 16) red_add_u32(buf + 2 * i + 1, x >> 16);
+        } else {
+            red_add_u32(buf + i, x);
+        }
+    }
+}
+
+// Writes merged counters buf of endpoints [lo, hi) into a cleared tile (origin org) at
+// its width; every count fits, since the width was chosen from a bound on the full count.
+template <int CW>
+__device__ void load_tile(uint32_t *tile, uint32_t org, uint32_t lo, uint32_t hi, const uint32_t *buf) {
+    const uint32_t words = tile_words_of<CW>(org, hi);
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) {
+        uint32_t x = 0;
+        if (CW == 0) {
+#pragma unroll
+            for (uint32_t b = 0; b < 4; ++b) {
+                const uint32_t w = org + 2 * i + (b >> 1);
+                if (w >= lo && w < hi) x |= __ldcg(buf + 2 * (w - lo) + (b & 1)) << (8 * b);
+            }
+        } else if (CW == 1) {
+            x = __ldcg(buf + 2 * i) | (__ldcg(buf + 2 * i + 1) << 16);
+        } else {
+            x = __ldcg(buf + i);
+        }
+        tile[i] = x;
+    }
+}
+
+template <int CW>
+__device__ __forceinline__ void clear_tile(uint32_t *tile, uint32_t org, uint32_t hi) {
+    const uint32_t words = tile_words_of<CW>(org, hi);
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) tile[i] = 0;
+}
+
+// The tile (X.lo, X.hi, width *cw) and the centre range [*pb, *pe) of centre-split item
+// `item`, with its record.
+__device__ void cs_setup(const DevGraph &G, const TileItem &item, int tile_words, SweepCtx &X,
+                         int64_t &pb, int64_t &pe, int &cw, CentreSplit &d) {
+    d = G.cs_desc[item.tile_begin];
+    const int a = item.anchor;
+    const int64_t sb = G.rowS_off[a], se = G.rowS_off[a + 1];
+    X.range_lo = G.orient_low ? 0u : (uint32_t)a + 1u;
+    X.range_hi = G.orient_low ? (uint32_t)a : (uint32_t)G.nS;
+    X.deg = se - sb;
+    X.row0 = sb;
+    X.single = false;
+    X.bbase = G.boff ? G.boff[a] : 0;
+    X.t = d.tile;
+    const int w = tile_width_of(item);
+    if (w == kWidthPerTile) {
+        const unsigned long long deg = (unsigned long long)X.deg;
+        const unsigned long long bound = deg < G.wl[a] ? deg : G.wl[a];
+        X.nt = var_tile_count(G.rowS_off, bound, X.range_lo, X.range_hi, (uint32_t)tile_words);
+        VarTile vt = var_tile_at(G.rowS_off, bound, X.range_lo, X.range_hi, (uint32_t)tile_words);
+        for (int t = 0; t < d.tile; ++t) vt = var_tile_at(G.rowS_off, bound, vt.hi, X.range_hi, (uint32_t)tile_words);
+        X.lo = vt.lo;
+        X.hi = vt.hi;
+        cw = vt.cw;
+    } else {
+        const uint32_t ept = endpoints_per_tile(w, (uint32_t)tile_words);
+        X.nt = (int)((X.range_hi - X.range_lo + ept - 1) / ept);
+        X.lo = X.range_lo + (uint32_t)d.tile * ept;
+        X.hi = min(X.lo + ept, X.range_hi);
+        cw = w;
+    }
+    pb = sb + X.deg * d.part / d.parts;
+    pe = sb + X.deg * (d.part + 1) / d.parts;
+}
+
+// The count pass of one part (inside the tile kernel). Without per-vertex output the
+// last part of the group completes the tile: bal / unb receive its pair totals.
+template <int CW, bool PF>
+__device__ void cs_count_part(const DevGraph &G, const SweepCtx &X, int64_t pb, int64_t pe,
+                              const CentreSplit &d, uint32_t *tile, ChunkSmem &cs, int *s_last,
+                              unsigned long long &bal, unsigned long long &unb) {
+    const BlockTile<CW> ctr(tile, X.lo);
+    unsigned long long carry = 0;
+    block_sweep<0, CW, BlockTile<CW>, PF>(G, pb, pe, X, ctr, cs, carry);
+    uint32_t *buf = G.cs_buf + (int64_t)d.group * G.cs_group_words;
+    const uint32_t org = BlockTile<CW>::origin(X.lo);
+    flush_tile<CW>(tile, org, X.lo, X.hi, buf);
+    if (G.bC) {
+        __syncthreads();
+        return;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) *s_last = atomicAdd(G.cs_arrive + d.group, 1u) == (unsigned)(d.parts - 1);
+    __syncthreads();
+    if (*s_last) {
+        __threadfence();
+        load_tile<CW>(tile, org, X.lo, X.hi, buf);
+        __syncthreads();
+        tile_epilogue<CW>(tile, org, X.hi, G.bS, bal, unb);
+    }
+    __syncthreads();
+}
+
+template <bool PF>
+__device__ void run_cs_count(const DevGraph &G, const TileItem &item, int tile_words, uint32_t *tile,
+                             ChunkSmem &cs, int *s_last, unsigned long long &bal, unsigned long long &unb) {
+    SweepCtx X;
+    int64_t pb, pe;
+    int cw;
+    CentreSplit d;
+    cs_setup(G, item, tile_words, X, pb, pe, cw, d);
+    switch (cw) {
+        case 0: cs_count_part<0, PF>(G, X, pb, pe, d, tile, cs, s_last, bal, unb); break;
+        case 1: cs_count_part<1, PF>(G, X, pb, pe, d, tile, cs, s_last, bal, unb); break;
+        default: cs_count_part<2, PF>(G, X, pb, pe, d, tile, cs, s_last, bal, unb); break;
+    }
+}
+
+// The centre pass of one part (per-vertex output, after the tile kernel): the merged
+// counts go into the tile, the part's slices are swept once more for their centres'
+// sums, and the last part of the group runs the epilogue (per-endpoint sums, totals).
+template <int CW, bool PF>
+__device__ void cs_centre_part(const DevGraph &G, const SweepCtx &X, int64_t pb, int64_t pe,
+                               const CentreSplit &d, uint32_t *tile, ChunkSmem &cs, int *s_last,
+                               unsigned long long &bal, unsigned long long &unb) {
+    const uint32_t org = BlockTile<CW>::origin(X.lo);
+    load_tile<CW>(tile, org, X.lo, X.hi, G.cs_buf + (int64_t)d.group * G.cs_group_words);
+    __syncthreads();
+    const BlockTile<CW> ctr(tile, X.lo);
+    unsigned long long carry = 0;
+    block_sweep<1, CW, BlockTile<CW>, PF>(G, pb, pe, X, ctr, cs, carry);
+    if (threadIdx.x == 0) *s_last = atomicAdd(G.cs_arrive + d.group, 1u) == (unsigned)(d.parts - 1);
+    __syncthreads();
+    if (*s_last)
+        tile_epilogue<CW>(tile, org, X.hi, G.bS, bal, unb);
+    else
+        clear_tile<CW>(tile, org, X.hi);
+    __syncthreads();
+}
+
 // Persistent blocks pop (anchor, tile range) items, heaviest first. PF: the graphs' rows
 // are much larger than L2 (slices are prefetched into L2 as their chunk is set up).
 template <bool PF>
@@ -939,7 +1120,7 @@ k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, 
     extern __shared__ uint4 smem_tile[];
     uint32_t *tile = reinterpret_cast<uint32_t *>(smem_tile);
     __shared__ ChunkSmem cs;
-    __shared__ int s_item;
+    __shared__ int s_item, s_last;
     __shared__ unsigned long long s_red[2][kTileWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < tile_words + kTileSlackWords; i += blockDim.x) tile[i] = 0;
@@ -960,11 +1141,15 @@ k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, 
         const DevGraph &G = graphs[item.graph];
         const long long t_start = item_cycles ? clock64() : 0;
         unsigned long long bal = 0, unb = 0;
-        switch (tile_width_of(item)) {
-            case 0: run_tile_item<0, PF>(G, item, tile_words, tile, cs, bal, unb); break;
-            case 1: run_tile_item<1, PF>(G, item, tile_words, tile, cs, bal, unb); break;
-            case 2: run_tile_item<2, PF>(G, item, tile_words, tile, cs, bal, unb); break;
-            default: run_tile_item_var<PF>(G, item, tile_words, tile, cs, bal, unb); break;
+        if (is_centre_split(item)) {
+            run_cs_count<PF>(G, item, tile_words, tile, cs, &s_last, bal, unb);
+        } else {
+            switch (tile_width_of(item)) {
+                case 0: run_tile_item<0, PF>(G, item, tile_words, tile, cs, bal, unb); break;
+                case 1: run_tile_item<1, PF>(G, item, tile_words, tile, cs, bal, unb); break;
+                case 2: run_tile_item<2, PF>(G, item, tile_words, tile, cs, bal, unb); break;
+                default: run_tile_item_var<PF>(G, item, tile_words, tile, cs, bal, unb); break;
+            }
         }
         bal = warp_sum(bal);
         unb = warp_sum(unb);
@@ -984,6 +1169,57 @@ k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, 
             if (G.bS && B) red_add(G.bS + item.anchor, B);
             // the item's duration on this SM (cost-model labels; off when NULL)
             if (item_cycles) item_cycles[it] = clock64() - t_start;
+        }
+    }
+}
+
+// Per-vertex output: the centre pass of every centre-split item (after the tile kernel
+// has merged all parts' counts), persistent blocks over the centre-split list.
+template <bool PF>
+__global__ void __launch_bounds__(kTileThreads, 2)
+k_tile_cs(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, int n_items,
+          unsigned *head, int tile_words) {
+    extern __shared__ uint4 smem_tile[];
+    uint32_t *tile = reinterpret_cast<uint32_t *>(smem_tile);
+    __shared__ ChunkSmem cs;
+    __shared__ int s_item, s_last;
+    __shared__ unsigned long long s_red[2][kTileWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < tile_words + kTileSlackWords; i += blockDim.x) tile[i] = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const TileItem item = items[it];
+        const DevGraph &G = graphs[item.graph];
+        SweepCtx X;
+        int64_t pb, pe;
+        int cw;
+        CentreSplit d;
+        cs_setup(G, item, tile_words, X, pb, pe, cw, d);
+        unsigned long long bal = 0, unb = 0;
+        switch (cw) {
+            case 0: cs_centre_part<0, PF>(G, X, pb, pe, d, tile, cs, &s_last, bal, unb); break;
+            case 1: cs_centre_part<1, PF>(G, X, pb, pe, d, tile, cs, &s_last, bal, unb); break;
+            default: cs_centre_part<2, PF>(G, X, pb, pe, d, tile, cs, &s_last, bal, unb); break;
+        }
+        bal = warp_sum(bal);
+        unb = warp_sum(unb);
+        if (lane == 0) {
+            s_red[0][warp] = bal;
+            s_red[1][warp] = unb;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long B = 0, U = 0;
+            for (int w = 0; w < kTileWarps; ++w) {
+                B += s_red[0][w];
+                U += s_red[1][w];
+            }
+            if (B) red_add(G.totals + 0, B);
+            if (U) red_add(G.totals + 1, U);
+            if (G.bS && B) red_add(G.bS + item.anchor, B);
         }
     }
 }
@@ -1296,6 +1532,7 @@ __device__ void run_motif_item(const DevGraph &G, const TileItem &item, int tile
     X.nt = (int)((X.range_hi - X.range_lo + ept - 1) / ept);
     X.single = se - sb <= kChunk;
     X.deg = se - sb;
+    X.row0 = sb;
     X.bbase = G.boff ? G.boff[a] : 0;
     unsigned long long carry = 0;  // unused: no centre pass
     for (int t = t0; t < t1; ++t) {
@@ -1377,7 +1614,8 @@ bbc_status configure_count_kernels() {
         cudaFuncAttributes fa{};
         int maxopt = 0;
         BBC_CUDA_TRY(cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        for (const void *f : {(const void *)k_tile<false>, (const void *)k_tile<true>}) {
+        for (const void *f : {(const void *)k_tile<false>, (const void *)k_tile<true>,
+                              (const void *)k_tile_cs<false>, (const void *)k_tile_cs<true>}) {
             BBC_CUDA_TRY(cudaFuncGetAttributes(&fa, f));
             if ((int)fa.sharedSizeBytes > tile_static_smem_bytes()) {
                 set_error("tile kernel static shared memory exceeds its budget");
@@ -1492,6 +1730,18 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
     if (fork) {
         BBC_TRY(side_streams(ss));
         BBC_CUDA_TRY(cudaEventRecord(ss->fork, st));
+    }
+    if (L.n_cs_items > 0) {
+        // the centre pass of the centre-split items, once the tile kernel has merged
+        // their counts (same stream)
+        const int tok = profile_begin(kProfTileCs, st);
+        note_launch();
+        auto kern = L.prefetch ? k_tile_cs<true> : k_tile_cs<false>;
+        kern<<<std::min(L.n_cs_items, sms * T.blocks_per_sm), kTileThreads,
+               (size_t)(T.tile_words + kTileSlackWords) * 4, st>>>(L.graphs, L.cs_items, L.n_cs_items,
+                                                                    &L.queue->cs_head, T.tile_words);
+        BBC_CUDA_TRY(cudaGetLastError());
+        profile_end(tok, st);
     }
     int side = 0;
     cudaStream_t main_st = st;

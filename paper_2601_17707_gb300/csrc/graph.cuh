@@ -40,6 +40,15 @@ struct bbc_graph {
     int32_t n_wt = 0;
     bbc::HashItem *gt_items = nullptr;
     int32_t n_gt = 0;
+    // centre-split tiles: per item its record, the items again (their centre pass), and
+    // per tile group the merged counters and an arrival counter
+    bbc::CentreSplit *cs_desc = nullptr;
+    bbc::TileItem *cs_items = nullptr;
+    int32_t n_cs_items = 0;
+    uint32_t *cs_buf = nullptr;
+    unsigned *cs_arrive = nullptr;
+    int64_t n_cs_groups = 0;
+    int64_t cs_group_words = 0;
 
     // count-time state
     bbc::DevGraph *dgraph = nullptr;       // device copy of the descriptor
@@ -63,5 +72,8 @@ void release_graph(bbc_graph *g, cudaStream_t st);
 DevGraph host_descriptor(const bbc_graph *g, bool per_vertex, bool with_bounds = false);
 // The graph's C -> S rows (4 bytes per edge) are larger than the device's L2.
 bool rows_exceed_l2(const bbc_graph *g);
+// Zeroes the merged counters and arrival counters of g's centre-split tiles (queued on
+// st); every launch of the tile kernel over g's items needs it first.
+bbc_status clear_centre_split(const bbc_graph *g, cudaStream_t st);
 
 }  // namespace bbc

@@ -40,7 +40,7 @@ __global__ void k_noalloc_setup(DevGraph d, NoallocHeader *h, unsigned long long
     h->graph = d;
     h->queue.tile_head = 0;
     h->queue.warp_head = 0;
-    h->queue.spare = 0;
+    h->queue.cs_head = 0;
     h->queue.error = 0;
     totals[0] = 0;
     totals[1] = 0;

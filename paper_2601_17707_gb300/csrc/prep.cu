@@ -239,21 +239,31 @@ struct ClassifyParams {
     int warp_tiles;            // single-tile anchors that fit a warp's table go to k_warp_tile
     int var_width;             // block tiles choose their counter width tile by tile
     int group_warps;           // warps per group-tile table (its capacity)
+    int centre_split;          // anchors heavier than their tiles can spread are split by centres too
 };
+
+// A centre-split tile is cut into parts of about split / kCentreSplitDiv wedges: finer than
+// the tile split, since these anchors are the ones that would otherwise end the launch
+// alone. Each part keeps at least kMinPartCentres centres.
+constexpr long long kCentreSplitDiv = 8;
+constexpr long long kMinPartCentres = 1024;
 
 // Work of one anchor: kind 0 none, 1 warp-hash item, 2 tile items, 3 warp-tile item (its
 // whole endpoint range fits one warp's counter table), 4 group-tile item (it fits a group
 // of warps' pooled table). For tiles: the counter width code (largest reachable count
 // min(degree, wedges) <= 255 / 65535 / more, or kWidthPerTile when the widths are chosen
 // tile by tile), the number of tiles over its endpoint range (not counted, and left at 1,
-// when count_tiles is false) and how many items they are split into.
+// when count_tiles is false), how many tile ranges they are split into, and into how many
+// centre parts each tile is cut (1, or >= 2 for a centre-split anchor: then every tile is
+// its own range and the anchor has groups * parts items).
 __device__ __forceinline__ void classify_one(const ClassifyParams &P, const int64_t *__restrict__ rowS_off,
                                              unsigned long long wl, int64_t deg, int a, int *kind, int *cw,
-                                             int *ntiles, int *groups, bool count_tiles = true) {
+                                             int *ntiles, int *groups, int *parts, bool count_tiles = true) {
     *kind = 0;
     *cw = 0;
     *ntiles = 0;
     *groups = 0;
+    *parts = 1;
     if (wl == 0 || deg < 2) return;
     if ((long long)wl <= P.warp_max) {
         *kind = 1;
@@ -294,6 +304,14 @@ __device__ __forceinline__ void classify_one(const ClassifyParams &P, const int6
     }
     long long g = 1;
     if ((long long)wl > P.split) g = ((long long)wl + P.split - 1) / P.split;
+    if (P.centre_split && count_tiles && g > nt) {
+        // more wedges than nt tile ranges of `split` each: cut every tile's centres too
+        const long long per_part = P.split / kCentreSplitDiv > 0 ? P.split / kCentreSplitDiv : 1;
+        long long k = ((long long)wl + (long long)nt * per_part - 1) / ((long long)nt * per_part);
+        if (k > kMaxParts) k = kMaxParts;
+        if (k > deg / kMinPartCentres) k = deg / kMinPartCentres;
+        if (k >= 2) *parts = (int)k;
+    }
     if (g > nt) g = nt;
     *kind = 2;
     *ntiles = nt;
@@ -303,13 +321,15 @@ __device__ __forceinline__ void classify_one(const ClassifyParams &P, const int6
 __global__ void k_classify(ClassifyParams P, const unsigned long long *__restrict__ wl,
                            const int64_t *__restrict__ rowS_off, int32_t *__restrict__ n_tile,
                            int32_t *__restrict__ n_warp, int64_t *__restrict__ n_bnd,
-                           int32_t *__restrict__ n_wt, int32_t *__restrict__ n_gt) {
+                           int32_t *__restrict__ n_wt, int32_t *__restrict__ n_gt,
+                           int32_t *__restrict__ n_csg) {
     for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < P.nS;
          a += (int64_t)gridDim.x * blockDim.x) {
-        int kind, cw, nt, g;
+        int kind, cw, nt, g, k;
         const int64_t deg = rowS_off[a + 1] - rowS_off[a];
-        classify_one(P, rowS_off, wl[a], deg, (int)a, &kind, &cw, &nt, &g);
-        n_tile[a] = kind == 2 ? g : 0;
+        classify_one(P, rowS_off, wl[a], deg, (int)a, &kind, &cw, &nt, &g, &k);
+        n_tile[a] = kind == 2 ? (k > 1 ? nt * k : g) : 0;
+        n_csg[a] = kind == 2 && k > 1 ? nt : 0;
         n_warp[a] = kind == 1 ? 1 : 0;
         n_wt[a] = kind == 3 ? 1 : 0;
         n_gt[a] = kind == 4 ? 1 : 0;
@@ -331,8 +351,8 @@ __global__ void k_tile_bounds(ClassifyParams P, const unsigned long long *__rest
          e += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t a = anchor_of[e];
         const int64_t sb = rowS_off[a], deg = rowS_off[a + 1] - sb;
-        int kind, cw, nt, g;
-        classify_one(P, rowS_off, wl[a], deg, (int)a, &kind, &cw, &nt, &g, false);
+        int kind, cw, nt, g, k;
+        classify_one(P, rowS_off, wl[a], deg, (int)a, &kind, &cw, &nt, &g, &k, false);
         if (kind != 2) continue;
         const uint32_t range_lo = P.orient_low ? 0u : a + 1u;
         const uint32_t range_hi = P.orient_low ? a : (uint32_t)P.nS;
@@ -374,14 +394,16 @@ __global__ void k_tile_bounds(ClassifyParams P, const unsigned long long *__rest
 __global__ void k_emit_items(ClassifyParams P, const unsigned long long *__restrict__ wl,
                              const int64_t *__restrict__ rowS_off, const int64_t *__restrict__ pos_tile,
                              const int64_t *__restrict__ pos_warp, const int64_t *__restrict__ pos_wt,
-                             const int64_t *__restrict__ pos_gt, TileItem *__restrict__ tiles,
+                             const int64_t *__restrict__ pos_gt, const int64_t *__restrict__ pos_csg,
+                             const int64_t *__restrict__ pos_csi, TileItem *__restrict__ tiles,
                              uint32_t *__restrict__ keys, HashItem *__restrict__ warp,
-                             HashItem *__restrict__ wt, HashItem *__restrict__ gt) {
+                             HashItem *__restrict__ wt, HashItem *__restrict__ gt,
+                             CentreSplit *__restrict__ cs_desc, TileItem *__restrict__ cs_items) {
     for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < P.nS;
          a += (int64_t)gridDim.x * blockDim.x) {
-        int kind, cw, nt, g;
+        int kind, cw, nt, g, k;
         const unsigned long long w = wl[a];
-        classify_one(P, rowS_off, w, rowS_off[a + 1] - rowS_off[a], (int)a, &kind, &cw, &nt, &g);
+        classify_one(P, rowS_off, w, rowS_off[a + 1] - rowS_off[a], (int)a, &kind, &cw, &nt, &g, &k);
         if (kind == 1) {
             warp[pos_warp[a]] = HashItem{0, (int32_t)a, (int32_t)w, 0};
         } else if (kind == 3 || kind == 4) {
@@ -390,6 +412,24 @@ __global__ void k_emit_items(ClassifyParams P, const unsigned long long *__restr
                 wt[pos_wt[a]] = h;
             else
                 gt[pos_gt[a]] = h;
+        } else if (kind == 2 && k > 1) {
+            // centre-split: item (tile t, part p) at t * k + p, in both lists; its record
+            // sits at the same index of the centre-split list
+            TileItem *dst = tiles + pos_tile[a];
+            uint32_t *kd = keys + pos_tile[a];
+            const double cost = (double)w / ((double)nt * k) + 1.0;
+            int q = (int)(log2(cost) * 1024.0);
+            q = q < 0 ? 0 : (q > 65535 ? 65535 : q);
+            for (int t = 0; t < nt; ++t) {
+                for (int p = 0; p < k; ++p) {
+                    const int64_t ci = pos_csi[a] + (int64_t)t * k + p;
+                    cs_desc[ci] = CentreSplit{t, (int16_t)p, (int16_t)k, (int32_t)(pos_csg[a] + t), 0};
+                    const TileItem it{0, (int32_t)a, (int32_t)ci, pack_tile_end(t + 1, cw) | kCentreSplitBit};
+                    dst[t * k + p] = it;
+                    kd[t * k + p] = 65535u - (uint32_t)q;
+                    cs_items[ci] = it;
+                }
+            }
         } else if (kind == 2) {
             TileItem *dst = tiles + pos_tile[a];
             uint32_t *kd = keys + pos_tile[a];
@@ -404,6 +444,14 @@ __global__ void k_emit_items(ClassifyParams P, const unsigned long long *__restr
             }
         }
     }
+}
+
+// Items on the centre-split list per anchor: all of a centre-split anchor's tile items.
+__global__ void k_cs_items(const int32_t *__restrict__ n_tile, const int32_t *__restrict__ n_csg,
+                           int32_t *__restrict__ n_csi, int64_t n) {
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n;
+         a += (int64_t)gridDim.x * blockDim.x)
+        n_csi[a] = n_csg[a] > 0 ? n_tile[a] : 0;
 }
 
 __global__ void k_iota(uint32_t *__restrict__ x, int64_t n) {
@@ -480,14 +528,25 @@ DevGraph host_descriptor(const bbc_graph *g, bool per_vertex, bool with_bounds) 
     d.rng = g->rng;
     d.bnd = with_bounds ? g->bnd : nullptr;
     d.boff = with_bounds ? g->boff : nullptr;
+    d.cs_desc = g->cs_desc;
+    d.cs_buf = g->cs_buf;
+    d.cs_arrive = g->cs_arrive;
+    d.cs_group_words = g->cs_group_words;
     return d;
+}
+
+bbc_status clear_centre_split(const bbc_graph *g, cudaStream_t st) {
+    if (g->n_cs_groups == 0) return BBC_OK;
+    BBC_CUDA_TRY(cudaMemsetAsync(g->cs_buf, 0, (size_t)(g->n_cs_groups * g->cs_group_words) * 4, st));
+    BBC_CUDA_TRY(cudaMemsetAsync(g->cs_arrive, 0, (size_t)g->n_cs_groups * 4, st));
+    return BBC_OK;
 }
 
 void release_graph(bbc_graph *g, cudaStream_t st) {
     if (!g) return;
     void *ptrs[] = {g->rowS_off, g->rowS, g->rowC_off, g->rowC, g->permS, g->permC, g->wl, g->rng, g->anchor_of, g->bnd, g->boff,
                     g->tile_items, g->warp_items, g->wt_items, g->gt_items, g->dgraph, g->bS, g->bC,
-                    g->totals, g->queue};
+                    g->totals, g->queue, g->cs_desc, g->cs_items, g->cs_buf, g->cs_arrive};
     for (void *p : ptrs)
         if (p) dev_free(p, st);
     delete g;
@@ -509,6 +568,16 @@ bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
     g->n_gt = 0;
     if (g->bnd) dev_free(g->bnd, st);
     if (g->boff) dev_free(g->boff, st);
+    if (g->cs_desc) dev_free(g->cs_desc, st);
+    if (g->cs_items) dev_free(g->cs_items, st);
+    if (g->cs_buf) dev_free(g->cs_buf, st);
+    if (g->cs_arrive) dev_free(g->cs_arrive, st);
+    g->cs_desc = nullptr;
+    g->cs_items = nullptr;
+    g->cs_buf = nullptr;
+    g->cs_arrive = nullptr;
+    g->n_cs_items = 0;
+    g->n_cs_groups = 0;
     g->tile_items = nullptr;
     g->warp_items = nullptr;
     g->bnd = nullptr;
@@ -523,8 +592,12 @@ bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
         return BBC_OK;
     }
     Scratch sc(st);
-    int32_t *nt = nullptr, *nh = nullptr, *nw = nullptr, *ng = nullptr;
-    int64_t *pt = nullptr, *ph = nullptr, *pw = nullptr, *pg = nullptr, *nb = nullptr;
+    int32_t *nt = nullptr, *nh = nullptr, *nw = nullptr, *ng = nullptr, *ncg = nullptr;
+    int64_t *pt = nullptr, *ph = nullptr, *pw = nullptr, *pg = nullptr, *nb = nullptr, *pcg = nullptr,
+            *pci = nullptr;
+    BBC_TRY(sc.get(&ncg, (size_t)nS));
+    BBC_TRY(sc.get(&pcg, (size_t)nS + 1));
+    BBC_TRY(sc.get(&pci, (size_t)nS + 1));
     BBC_TRY(sc.get(&nt, (size_t)nS));
     BBC_TRY(sc.get(&nh, (size_t)nS));
     BBC_TRY(sc.get(&nw, (size_t)nS));
@@ -536,10 +609,49 @@ bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
     BBC_TRY(sc.get(&nb, (size_t)nS));
     BBC_TRY(dev_alloc_n(&g->boff, (size_t)nS + 1, st));
     ClassifyParams P{g->nS, g->orient_low, t.tile_words, t.warp_max_wedges, t.split_wedges,
-                     (t.plain || t.tiles_only) ? 0 : 1, t.tiles_only ? 0 : 1, t.group_warps};
-    note_launch();
-    k_classify<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, nt, nh, nb, nw, ng);
-    BBC_LAUNCH_CHECK("k_classify");
+                     (t.plain || t.tiles_only) ? 0 : 1, t.tiles_only ? 0 : 1, t.group_warps,
+                     (t.plain || t.tiles_only) ? 0 : 1};
+    // one tile group's merged counters: two per endpoint of the widest tile
+    const int64_t group_words = 2 * (int64_t)tile_endpoints(0, (uint32_t)t.tile_words);
+    int64_t n_csg = 0;
+    for (;;) {
+        note_launch();
+        k_classify<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, nt, nh, nb, nw, ng, ncg);
+        BBC_LAUNCH_CHECK("k_classify");
+        if (!P.centre_split) break;
+        BBC_TRY(exclusive_scan_i32_to_i64(ncg, pcg, nS, st));
+        BBC_CUDA_TRY(cudaMemcpyAsync(&n_csg, pcg + nS, 8, cudaMemcpyDeviceToHost, st));
+        BBC_CUDA_TRY(cudaStreamSynchronize(st));
+        // the merge buffers stay below 8 bytes per edge (and 16 MiB for small graphs);
+        // past that the anchors keep their tile split only
+        const int64_t cap = std::max<int64_t>(int64_t(16) << 20, 8 * g->n_edges);
+        if (n_csg * group_words * 4 <= cap) break;
+        P.centre_split = 0;
+        n_csg = 0;
+    }
+    int64_t n_csi = 0;
+    if (n_csg > 0) {
+        // a centre-split anchor's items (all of its n_tile) also form the centre-split list
+        int32_t *nci = nullptr;
+        BBC_TRY(sc.get(&nci, (size_t)nS));
+        note_launch();
+        k_cs_items<<<grid_for(nS), kThreads, 0, st>>>(nt, ncg, nci, nS);
+        BBC_LAUNCH_CHECK("k_cs_items");
+        BBC_TRY(exclusive_scan_i32_to_i64(nci, pci, nS, st));
+        BBC_CUDA_TRY(cudaMemcpyAsync(&n_csi, pci + nS, 8, cudaMemcpyDeviceToHost, st));
+        BBC_CUDA_TRY(cudaStreamSynchronize(st));
+        if (n_csi > INT32_MAX) {
+            set_error("work list longer than 2^31 items");
+            return BBC_E_INVALID_ARG;
+        }
+        BBC_TRY(dev_alloc_n(&g->cs_desc, (size_t)n_csi, st));
+        BBC_TRY(dev_alloc_n(&g->cs_items, (size_t)n_csi, st));
+        BBC_TRY(dev_alloc_n(&g->cs_buf, (size_t)(n_csg * group_words), st));
+        BBC_TRY(dev_alloc_n(&g->cs_arrive, (size_t)n_csg, st));
+        g->n_cs_items = (int32_t)n_csi;
+        g->n_cs_groups = n_csg;
+        g->cs_group_words = group_words;
+    }
     BBC_TRY(exclusive_scan_i32_to_i64(nt, pt, nS, st));
     BBC_TRY(exclusive_scan_i32_to_i64(nh, ph, nS, st));
     BBC_TRY(exclusive_scan_i32_to_i64(nw, pw, nS, st));
@@ -581,8 +693,9 @@ bbc_status build_work_lists(bbc_graph *g, const Tuning &t, cudaStream_t st) {
     BBC_TRY(dev_alloc_n(&g->tile_items, (size_t)ntile, st));
     g->n_tile = (int32_t)ntile;
     note_launch();
-    k_emit_items<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, pt, ph, pw, pg, raw, keys,
-                                                     g->warp_items, g->wt_items, g->gt_items);
+    k_emit_items<<<grid_for(nS), kThreads, 0, st>>>(P, g->wl, g->rowS_off, pt, ph, pw, pg, pcg, pci, raw, keys,
+                                                     g->warp_items, g->wt_items, g->gt_items, g->cs_desc,
+                                                     g->cs_items);
     BBC_LAUNCH_CHECK("k_emit_items");
     // Order the tile items by expected cost, largest first (the plain schedule keeps
     // rank order).

@@ -181,6 +181,9 @@ void prep_main(bbc_server *S) {
         bbc_status s = prepare_graph(r->n_u, r->n_v, r->n_edges, r->u.data(), r->v.data(),
                                      r->s.data(), 0u, st, &g);
         if (s == BBC_OK) s = build_work_lists(g, S->tuning, st);
+        // centre-split parts of one tile may run in different ticks: their merged
+        // counters are cleared once, here
+        if (s == BBC_OK) s = clear_centre_split(g, st);
         if (s == BBC_OK) {
             cudaError_t e = cudaMemsetAsync(g->totals, 0, 16, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
