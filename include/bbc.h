@@ -75,7 +75,7 @@ typedef struct bbc_tuning {
                                   tile-range items that run on different blocks; an
                                   anchor heavier than split_wedges times its tiles also
                                   has each tile's centres cut into parts (up to 64, of
-                                  about split_wedges / 8 wedges) whose counts are merged
+                                  about split_wedges / 16 wedges) whose counts are merged
                                   in device memory (at most the larger of 8 bytes per
                                   edge and 16 MiB, else no centre split) */
     int32_t blocks_per_sm;     /* resident blocks per SM of the tile kernel (1 or 2) */

@@ -289,6 +289,7 @@ bbc_status count_graph(bbc_graph *g, uint64_t *totals_dev, uint64_t *per_u, uint
     if (pv) {
         L.cs_items = g->cs_items;
         L.n_cs_items = g->n_cs_items;
+        L.per_vertex = true;
     }
     BBC_TRY(launch_count(L, st));
     if (pv) {

@@ -256,6 +256,7 @@ struct CountLaunch {
     // the tile kernel (the graphs' cs_buf and cs_arrive zeroed by the caller)
     const TileItem *cs_items = nullptr;
     int32_t n_cs_items = 0;
+    bool per_vertex = false;    // the graphs count per-vertex sums (picks the tile schedule)
 };
 
 // One contiguous run of a graph's work items to copy into a combined list, tagged with

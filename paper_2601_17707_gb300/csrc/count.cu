@@ -29,6 +29,7 @@
 // a - c - w of type t lies in (count_t(a, w) - 1) balanced butterflies through c, so a
 // second sweep over the same slices, after the counters are complete, adds that to b(c).
 #include <algorithm>
+#include <climits>
 #include <type_traits>
 
 #include "graph.cuh"
@@ -44,6 +45,9 @@ constexpr int kLongMin = 64;              // slices this long are cut into piece
 // the chunk scan packs a chunk's short-slice wedges into 16 bits
 static_assert((kLongMin - 1) * kChunk < (1 << 16), "short-slice wedges of a chunk exceed the scan field");
 constexpr int kPiece = 1024;              // wedges per piece of a long slice
+// how the tile kernel's blocks take items: rank order by block index (Algorithm 3's static
+// mapping), the atomic queue, or the queue with the next item taken one item early
+enum { kScheduleQueue = 0, kScheduleStatic = 1, kScheduleQueueAhead = 2 };
 constexpr int kLongSlice = 64;            // warp sweep: slices this long use the whole warp
 constexpr int kWtThreads = 512;          // warp-tile kernel: 16 warps, one table each
 constexpr int kWtWarps = kWtThreads / 32;
@@ -394,10 +398,10 @@ __device__ __forceinline__ void wedge_any(const Ctr &ctr, uint32_t x, uint32_t s
 // slice j's first entry minus sP[j], and smeta[j] holds the anchor edge's sign bit and a
 // tag below 2^31. A lane's slice is the window's first slice plus the number of slice
 // starts at or before its position, counted from a bit mask of the starts inside the
-// window. The next window's entry is loaded before this window's counters are touched,
-// so two loads per lane are in flight. MODE 1 hands each run of lanes on one slice, once
-// per window, to add(tag, sum over its wedges of count - 1).
-template <int MODE, class A, class Ctr, class Add>
+// window. The entries of the next AHEAD (1 or 2) windows are loaded before this window's
+// counters are touched, so AHEAD + 1 loads per lane are in flight. MODE 1 hands each run
+// of lanes on one slice, once per window, to add(tag, sum over its wedges of count - 1).
+template <int MODE, class A, int AHEAD, class Ctr, class Add>
 __device__ __forceinline__ void walk_short(const Ctr &ctr, const uint32_t *__restrict__ rowC,
                                            const uint32_t *sP, const uint32_t *sbase,
                                            const uint32_t *smeta, int nz, uint32_t r0, uint32_t r1,
@@ -415,23 +419,34 @@ __device__ __forceinline__ void walk_short(const Ctr &ctr, const uint32_t *__res
         j = r + (uint32_t)lane < r1 ? jbase + __popc(m & ((2u << lane) - 1u)) : -1;
         jnext = jbase + __popc(m) + (at32 ? 1 : 0);
     };
-    uint32_t m = 0, x = 0, meta = 0;
-    int j = -1, jn = 0;
-    locate(r0, last_le_n(sP, nz, r0), m, j, jn);
-    if (j >= 0) {
-        meta = smeta[j];
-        x = __ldg(rowC + (uint32_t)(sbase[j] + r0 + lane));
-    }
-    for (uint32_t r = r0; r < r1; r += 32u) {
-        uint32_t m2 = 0, x2 = 0, meta2 = 0;
-        int j2 = -1, jn2 = jn;
-        if (r + 32u < r1) {
-            locate(r + 32u, jn, m2, j2, jn2);
-            if (j2 >= 0) {
-                meta2 = smeta[j2];
-                x2 = __ldg(rowC + (uint32_t)(sbase[j2] + r + 32u + lane));
+    // one window's slice mask, lane slice, sign/tag and entry, loaded AHEAD windows
+    // before it is used
+    struct Stage {
+        uint32_t m = 0, x = 0, meta = 0;
+        int j = -1;
+    };
+    auto fetch = [&](uint32_t r, int jbase, Stage &st, int &jnext) {
+        st = Stage{};
+        jnext = jbase;
+        if (r < r1) {
+            locate(r, jbase, st.m, st.j, jnext);
+            if (st.j >= 0) {
+                st.meta = smeta[st.j];
+                st.x = __ldg(rowC + (uint32_t)(sbase[st.j] + r + lane));
             }
         }
+    };
+    Stage s0, s1, s2;
+    int jn = 0;
+    fetch(r0, last_le_n(sP, nz, r0), s0, jn);
+    if (AHEAD == 2) fetch(r0 + 32u, jn, s1, jn);
+    for (uint32_t r = r0; r < r1; r += 32u) {
+        if (AHEAD == 2)
+            fetch(r + 64u, jn, s2, jn);
+        else
+            fetch(r + 32u, jn, s1, jn);
+        const uint32_t m = s0.m, x = s0.x, meta = s0.meta;
+        const int j = s0.j;
         A v = 0;
         if (j >= 0) {
             wedge_any<MODE>(ctr, x, Ctr::sign_key(meta & kSignBit), v);
@@ -459,11 +474,8 @@ __device__ __forceinline__ void walk_short(const Ctr &ctr, const uint32_t *__res
             const int jnb = __shfl_down_sync(kFull, j, 1);
             if (j >= 0 && (lane == 31 || jnb != j) && v) add(meta & kIdMask, v);
         }
-        m = m2;
-        j = j2;
-        jn = jn2;
-        x = x2;
-        meta = meta2;
+        s0 = s1;
+        if (AHEAD == 2) s1 = s2;
     }
 }
 
@@ -478,22 +490,26 @@ struct WarpStage {
 // One warp's pass over all oriented wedges of anchor rows [sb, se) (the warp kernels'
 // sweep: their anchors fit one counter table). MODE 0 bumps the counters; MODE 1 (the
 // per-vertex centre pass) reads them and adds (count - 1) per wedge to the centre's b.
-// Warps take batches of `batch` (<= 32) centres from *batch_ctr; lane j owns centre j's
-// slice. Long
+// Warps take batches of `batch` (<= 32) centres from *batch_ctr (or, with batch_ctr NULL,
+// one warp takes them all in order); lane j owns centre j's slice. Long
 // slices are swept by the whole warp with 16-byte loads; short ones are compacted into
-// the warp's stage and walked lane-interleaved (walk_short). Per-centre sums of a batch
-// stay below 2^32: a slice's counts add up to at most the number of edges.
-template <int MODE, class Counter>
+// the warp's stage and walked lane-interleaved (walk_short, AHEAD windows loaded ahead:
+// the hash kernel keeps one for its registers). Per-centre sums of a batch stay below
+// 2^32: a slice's counts add up to at most the number of edges.
+template <int MODE, int AHEAD = 2, class Counter>
 __device__ __forceinline__ void warp_sweep(const DevGraph &G, int64_t sb, int64_t se,
                                       const Counter &ctr, int *batch_ctr, uint32_t *sacc,
                                       WarpStage &ws, int batch = 32) {
     const int lane = threadIdx.x & 31;
     const int64_t nbatch = (se - sb + batch - 1) / batch;
+    int next_private = 0;   // a warp alone on its anchor (batch_ctr NULL) takes every batch
     const uint32_t *__restrict__ rowC = G.rowC;
     for (;;) {
-        int bi = 0;
-        if (lane == 0) bi = atomicAdd(batch_ctr, 1);
-        bi = __shfl_sync(kFull, bi, 0);
+        int bi = next_private++;
+        if (batch_ctr) {
+            if (lane == 0) bi = atomicAdd(batch_ctr, 1);
+            bi = __shfl_sync(kFull, bi, 0);
+        }
         if (bi >= nbatch) break;
         const int64_t ci = sb + (int64_t)bi * batch + lane;
         uint32_t b = 0, len = 0, sg = 0, c = 0;
@@ -570,7 +586,7 @@ __device__ __forceinline__ void warp_sweep(const DevGraph &G, int64_t sb, int64_
         if (MODE == 1) sacc[lane] = 0;
         __syncwarp();
         if (total)
-            walk_short<MODE, uint32_t>(ctr, rowC, ws.sP, ws.sbase, ws.meta, nzs, 0u, total,
+            walk_short<MODE, uint32_t, AHEAD>(ctr, rowC, ws.sP, ws.sbase, ws.meta, nzs, 0u, total,
                                        [&](uint32_t tag, uint32_t v) { atomicAdd(sacc + tag, v); });
         __syncwarp();
         if (MODE == 1) {
@@ -721,7 +737,7 @@ __device__ void block_sweep(const DevGraph &G, int64_t sb, int64_t se, const Swe
             const uint32_t r0 = (uint32_t)(((unsigned long long)NS * warp) / kTileWarps);
             const uint32_t r1 = (uint32_t)(((unsigned long long)NS * (warp + 1)) / kTileWarps);
             if (r0 < r1)
-                walk_short<MODE, Acc<CW>>(ctr, rowC, cs.sP, cs.sbase, cs.smeta, (int)cs.nz, r0, r1,
+                walk_short<MODE, Acc<CW>, 2>(ctr, rowC, cs.sP, cs.sbase, cs.smeta, (int)cs.nz, r0, r1,
                                           [&](uint32_t tag, Acc<CW> v) { acc_add<CW>(cs, (int)tag, v); });
         }
         // long slices: warp w sweeps pieces w, w + 16, w + 32, ... (pieces are at most
@@ -880,7 +896,9 @@ __device__ void run_tile_item(const DevGraph &G, const TileItem &item, int tile_
         block_sweep<0, CW, BlockTile<CW>, PF>(G, sb, se, X, ctr, cs, centre_carry);
         if (G.bC) block_sweep<1, CW, BlockTile<CW>, PF>(G, sb, se, X, ctr, cs, centre_carry);
         tile_epilogue<CW>(tile, BlockTile<CW>::origin(X.lo), X.hi, G.bS, bal, unb);
-        __syncthreads();
+        // the next tile's sweep must not bump words the epilogue is still clearing; after
+        // the last tile the kernel's item barrier does that
+        if (t + 1 < t1) __syncthreads();
     }
     if (centre_carry) red_add(G.bC + (cs.ent[threadIdx.x] & kIdMask), centre_carry);
 }
@@ -890,12 +908,12 @@ __device__ void run_tile_item(const DevGraph &G, const TileItem &item, int tile_
 template <int CW, bool PF>
 __device__ void tile_pass(const DevGraph &G, int64_t sb, int64_t se, const SweepCtx &X, uint32_t *tile,
                           ChunkSmem &cs, unsigned long long &centre_carry, unsigned long long &bal,
-                          unsigned long long &unb) {
+                          unsigned long long &unb, bool last) {
     const BlockTile<CW> ctr(tile, X.lo);
     block_sweep<0, CW, BlockTile<CW>, PF>(G, sb, se, X, ctr, cs, centre_carry);
     if (G.bC) block_sweep<1, CW, BlockTile<CW>, PF>(G, sb, se, X, ctr, cs, centre_carry);
     tile_epilogue<CW>(tile, BlockTile<CW>::origin(X.lo), X.hi, G.bS, bal, unb);
-    __syncthreads();
+    if (!last) __syncthreads();   // (see run_tile_item)
 }
 
 // An item whose tiles choose their counter width one by one (the tile boundaries are the
@@ -923,10 +941,11 @@ __device__ void run_tile_item_var(const DevGraph &G, const TileItem &item, int t
         X.t = t;
         X.lo = vt.lo;
         X.hi = vt.hi;
+        const bool last = t + 1 == t1;
         switch (vt.cw) {
-            case 0: tile_pass<0, PF>(G, sb, se, X, tile, cs, centre_carry, bal, unb); break;
-            case 1: tile_pass<1, PF>(G, sb, se, X, tile, cs, centre_carry, bal, unb); break;
-            default: tile_pass<2, PF>(G, sb, se, X, tile, cs, centre_carry, bal, unb); break;
+            case 0: tile_pass<0, PF>(G, sb, se, X, tile, cs, centre_carry, bal, unb, last); break;
+            case 1: tile_pass<1, PF>(G, sb, se, X, tile, cs, centre_carry, bal, unb, last); break;
+            default: tile_pass<2, PF>(G, sb, se, X, tile, cs, centre_carry, bal, unb, last); break;
         }
         if (t + 1 < t1) vt = var_tile_at(G.rowS_off, bound, vt.hi, X.range_hi, (uint32_t)tile_words);
     }
@@ -1116,26 +1135,42 @@ __device__ void cs_centre_part(const DevGraph &G, const SweepCtx &X, int64_t pb,
 template <bool PF>
 __global__ void __launch_bounds__(kTileThreads, 2)
 k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, int n_items,
-       unsigned *head, int tile_words, int static_schedule, long long *item_cycles) {
+       unsigned *head, int tile_words, int schedule, long long *item_cycles) {
+    const bool static_schedule = schedule == kScheduleStatic;
     extern __shared__ uint4 smem_tile[];
     uint32_t *tile = reinterpret_cast<uint32_t *>(smem_tile);
     __shared__ ChunkSmem cs;
-    __shared__ int s_item, s_last;
+    __shared__ int s_item[2], s_last;
     __shared__ unsigned long long s_red[2][kTileWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < tile_words + kTileSlackWords; i += blockDim.x) tile[i] = 0;
     int next_static = blockIdx.x;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            if (static_schedule) {
-                s_item = next_static;
-                next_static += gridDim.x;
-            } else {
-                s_item = (int)atomicAdd(head, 1u);
-            }
+    // Thread 0 publishes the next item before the barrier that ends the current one, so
+    // that one barrier serves both (the slots alternate, so the write never meets a read
+    // of the current item's slot). With kScheduleQueueAhead, past the queue's heavy head
+    // it also takes the item after that one item early, so that the atomic's latency
+    // hides behind the work; near the head a block holding a second heavy item would end
+    // the launch late (and with per-vertex counts, whose items take twice as long, it
+    // measured slower throughout).
+    auto pop = [&]() -> int {
+        if (static_schedule) {
+            const int i = next_static;
+            next_static += gridDim.x;
+            return i;
         }
-        __syncthreads();
-        const int it = s_item;
+        return (int)atomicAdd(head, 1u);
+    };
+    const int deep = schedule == kScheduleQueueAhead ? 8 * (int)gridDim.x : INT_MAX;
+    int ahead = -1;
+    if (threadIdx.x == 0) s_item[0] = pop();
+    auto take = [&](int slot) {
+        const int nx = ahead >= 0 ? ahead : pop();
+        s_item[slot] = nx;
+        ahead = nx >= deep ? pop() : -1;
+    };
+    __syncthreads();
+    for (int slot = 0;; slot ^= 1) {
+        const int it = s_item[slot];
         if (it >= n_items) break;
         const TileItem item = items[it];
         const DevGraph &G = graphs[item.graph];
@@ -1157,6 +1192,7 @@ k_tile(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ items, 
             s_red[0][warp] = bal;
             s_red[1][warp] = unb;
         }
+        if (threadIdx.x == 0) take(slot ^ 1);
         __syncthreads();
         if (threadIdx.x == 0) {
             unsigned long long B = 0, U = 0;
@@ -1224,12 +1260,11 @@ k_tile_cs(const DevGraph *__restrict__ graphs, const TileItem *__restrict__ item
     }
 }
 
-__global__ void __launch_bounds__(kHashThreads)
+__global__ void __launch_bounds__(kHashThreads, 5)
 k_warp_hash(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ items, int n_items,
             QueueState *q, int chunk, int slots_lg) {
     extern __shared__ uint4 smem_hash[];
     __shared__ uint32_t s_acc[kHashWarps][32];
-    __shared__ int s_batch[kHashWarps];
     __shared__ WarpStage s_stage[kHashWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // each warp's table holds 2^slots_lg slots: twice the largest wedge count of the
@@ -1260,14 +1295,10 @@ k_warp_hash(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ it
         int lg = 6;
         while ((1 << lg) < 2 * item.wedges && lg < slots_lg) ++lg;
         const HashCounter ctr{keys, vals, (1u << lg) - 1u, 32 - lg, &q->error};
-        if (lane == 0) s_batch[warp] = 0;
-        __syncwarp();
-        warp_sweep<0>(G, sb, se, ctr, &s_batch[warp], nullptr, s_stage[warp]);
+        warp_sweep<0, 1>(G, sb, se, ctr, nullptr, nullptr, s_stage[warp]);
         __syncwarp();
         if (G.bC) {
-            if (lane == 0) s_batch[warp] = 0;
-            __syncwarp();
-            warp_sweep<1>(G, sb, se, ctr, &s_batch[warp], s_acc[warp], s_stage[warp]);
+            warp_sweep<1, 1>(G, sb, se, ctr, nullptr, s_acc[warp], s_stage[warp]);
             __syncwarp();
         }
         unsigned long long bal = 0, unb = 0;
@@ -1365,12 +1396,13 @@ __device__ void group_tile_item(const DevGraph &G, int a, uint32_t *tile, int gr
     // some: an anchor of few centres with long rows would otherwise keep one warp busy
     const int64_t per_warp = (se - sb + GW - 1) / GW;
     const int batch = GW == 1 ? 32 : (per_warp < 4 ? 4 : (per_warp > 32 ? 32 : (int)per_warp));
-    warp_sweep<0>(G, sb, se, ctr, batch_ctr, nullptr, ws, batch);
+    int *const bc = GW == 1 ? nullptr : batch_ctr;   // a single warp takes its batches in order
+    warp_sweep<0>(G, sb, se, ctr, bc, nullptr, ws, batch);
     group_sync<GW>(grp);
     if (G.bC) {
         if (gt == 0) *batch_ctr = 0;
         group_sync<GW>(grp);
-        warp_sweep<1>(G, sb, se, ctr, batch_ctr, sacc, ws, batch);
+        warp_sweep<1>(G, sb, se, ctr, bc, sacc, ws, batch);
         group_sync<GW>(grp);
     }
     const uint32_t n = hi - lo;
@@ -1423,11 +1455,22 @@ k_group_tile(const DevGraph *__restrict__ graphs, const HashItem *__restrict__ i
     const int gt = threadIdx.x - grp * GW * 32;
     uint32_t *tile = reinterpret_cast<uint32_t *>(smem_wt) + grp * (GW * kWtWords);
     for (int i = gt; i < GW * kWtWords; i += GW * 32) tile[i] = 0;
-    // items come `chunk` at a time from the queue (see k_warp_hash)
+    // items come `chunk` at a time from the queue (see k_warp_hash); a group of several
+    // warps has its first thread take each chunk one chunk early, so that the atomic's
+    // latency hides behind the current items (single warps measured slower that way)
     int it = 0, it_end = 0;
+    int ahead = 0;
+    if (GW > 1 && gt == 0) ahead = (int)atomicAdd(head, (unsigned)chunk);
     for (;; ++it) {
         if (it >= it_end) {
-            if (gt == 0) s_item[grp] = (int)atomicAdd(head, (unsigned)chunk);
+            if (gt == 0) {
+                if (GW > 1) {
+                    s_item[grp] = ahead;
+                    ahead = (int)atomicAdd(head, (unsigned)chunk);
+                } else {
+                    s_item[grp] = (int)atomicAdd(head, (unsigned)chunk);
+                }
+            }
             group_sync<GW>(grp);
             it = s_item[grp];
             it_end = min(it + chunk, n_items);
@@ -1716,8 +1759,9 @@ bbc_status launch_count(const CountLaunch &L, cudaStream_t st) {
         // schedule: one block per item
         const int grid = T.plain ? L.n_tile_items : std::min(L.n_tile_items, sms * T.blocks_per_sm);
         auto kern = L.prefetch ? k_tile<true> : k_tile<false>;
+        const int schedule = T.plain ? kScheduleStatic : (L.per_vertex ? kScheduleQueue : kScheduleQueueAhead);
         kern<<<grid, kTileThreads, (size_t)(T.tile_words + kTileSlackWords) * 4, st>>>(
-            L.graphs, L.tile_items, L.n_tile_items, &L.queue->tile_head, T.tile_words, T.plain,
+            L.graphs, L.tile_items, L.n_tile_items, &L.queue->tile_head, T.tile_words, schedule,
             L.item_cycles);
         BBC_CUDA_TRY(cudaGetLastError());
         profile_end(tok, st);
@@ -1822,7 +1866,7 @@ bbc_status launch_tile_only(const DevGraph *graphs, const TileItem *items, int n
     if (n_items <= 0) return BBC_OK;
     note_launch();
     k_tile<false><<<blocks, kTileThreads, (size_t)(tile_words + kTileSlackWords) * 4, st>>>(graphs, items, n_items, head,
-                                                                 tile_words, 0, nullptr);
+                                                                 tile_words, kScheduleQueue, nullptr);
     BBC_CUDA_TRY(cudaGetLastError());
     return BBC_OK;
 }

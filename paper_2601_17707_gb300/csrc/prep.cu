@@ -245,7 +245,7 @@ struct ClassifyParams {
 // A centre-split tile is cut into parts of about split / kCentreSplitDiv wedges: finer than
 // the tile split, since these anchors are the ones that would otherwise end the launch
 // alone. Each part keeps at least kMinPartCentres centres.
-constexpr long long kCentreSplitDiv = 8;
+constexpr long long kCentreSplitDiv = 16;
 constexpr long long kMinPartCentres = 1024;
 
 // Work of one anchor: kind 0 none, 1 warp-hash item, 2 tile items, 3 warp-tile item (its
