@@ -304,8 +304,9 @@ __device__ __forceinline__ void classify_one(const ClassifyParams &P, const int6
     }
     long long g = 1;
     if ((long long)wl > P.split) g = ((long long)wl + P.split - 1) / P.split;
-    if (P.centre_split && count_tiles && g > nt) {
-        // more wedges than nt tile ranges of `split` each: cut every tile's centres too
+    if (P.centre_split && count_tiles && 2 * g > nt) {
+        // more wedges than nt tile ranges of half a `split` each: cut every tile's
+        // centres too
         const long long per_part = P.split / kCentreSplitDiv > 0 ? P.split / kCentreSplitDiv : 1;
         long long k = ((long long)wl + (long long)nt * per_part - 1) / ((long long)nt * per_part);
         if (k > kMaxParts) k = kMaxParts;
