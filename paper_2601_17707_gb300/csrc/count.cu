@@ -16,6 +16,9 @@
 //     of centre c in the window are one contiguous slice. Per chunk of 512 centres, the
 //     short slices are swept by warps with lanes on consecutive positions, and the long
 //     ones in 1,024-wedge pieces with 16-byte loads.
+//     An anchor too heavy for its tiles to spread over the blocks has each tile's
+//     centres cut into parts whose counts merge in device memory; with per-vertex
+//     output, k_tile_cs then runs those parts' centre passes.
 //   * k_group_tile<4> / k_group_tile<1>: anchors whose whole endpoint range fits a
 //     4-warp group's or one warp's table.
 //   * k_warp_hash: light anchors (few wedges) get one warp each and a small open-
