@@ -355,13 +355,22 @@ def bench_dynamic(g, sizes=(10, 100, 1000)):
     return [bench_dynamic_batch(g, n, seed=7 + i) for i, n in enumerate(sizes)]
 
 
+def tile_path_time(prof):
+    """(launches, total ms) of the tile path in a per-kernel profile: the k_tile launches,
+    with the k_tile_cs launches (the centre passes of centre-split tiles, one after each
+    per-vertex k_tile launch of such a graph) added to their time."""
+    n, ms = prof.get("k_tile", (0, 0.0))
+    return n, ms + prof.get("k_tile_cs", (0, 0.0))[1]
+
+
 def per_kernel_roofline(work, prof, passes, peak):
     """{kernel: achieved GB/s and fraction of `peak`} from the work behind each path
     (wedges and pair-side edges of its anchors; 4 B per wedge visit, `passes` visits per
-    wedge, 20 B per edge) and its CUDA-event time per launch."""
+    wedge, 20 B per edge) and its CUDA-event time per launch (the tile path's time is
+    k_tile's plus k_tile_cs's)."""
     out = {}
     for k, (items, wedges, edges) in work.items():
-        n, ms = prof.get(k, (0, 0.0))
+        n, ms = tile_path_time(prof) if k == "k_tile" else prof.get(k, (0, 0.0))
         if not n or not items:
             continue
         alg = 4 * passes * wedges + 20 * edges
@@ -707,7 +716,7 @@ def single_graph(args, workload, steps, warmup, dev, dist, world, with_e2e):
     cs_launches, cs_ms = prof.get("k_tile_cs", (0, 0.0))
     if tile_launches:
         alg_bytes = 4 * 2 * W + 20 * g.n_edges   # per launch (one launch per step)
-        path_ms = (tile_ms + cs_ms) / tile_launches
+        path_ms = tile_path_time(prof)[1] / tile_launches
         achieved = alg_bytes / (path_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": recorded_traffic(workload),

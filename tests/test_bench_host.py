@@ -1,6 +1,6 @@
 """Host-side helpers of bench.py that need no GPU: the digest that ties the committed DRAM
-traffic record to the tile kernel's code, and the lookup that drops the record once that
-code changes.
+traffic record to the tile kernel's code, the lookup that drops the record once that
+code changes, and the tile path's time (k_tile plus the centre-split launch).
 """
 
 from __future__ import annotations
@@ -33,3 +33,15 @@ def test_traffic_record_follows_the_kernel_digest(tmp_path, monkeypatch):
     assert bench.recorded_traffic("uniform_2k_3k") is None
     path.write_text(json.dumps(dict(rec, source_sha256="0" * 64)))
     assert bench.recorded_traffic() is None
+
+
+def test_tile_path_adds_the_centre_split_launch():
+    prof = {"k_tile": (2, 80.0), "k_tile_cs": (2, 20.0), "k_warp_hash": (2, 4.0)}
+    assert bench.tile_path_time(prof) == (2, 100.0)
+    assert bench.tile_path_time({"k_tile": (3, 30.0)}) == (3, 30.0)
+    work = {"k_tile": (10, 1_000_000, 100), "k_warp_hash": (5, 1_000, 10)}
+    r = bench.per_kernel_roofline(work, prof, 2, 1000.0)
+    # 4 B x 2 visits x 10^6 wedges + 20 B x 100 edges over 50 ms per launch
+    assert r["k_tile"]["ms_per_launch"] == 50.0
+    assert abs(r["k_tile"]["achieved_gbs"] - 8_002_000 / 0.05 / 1e9) < 1e-12
+    assert r["k_warp_hash"]["ms_per_launch"] == 2.0
