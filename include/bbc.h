@@ -73,8 +73,8 @@ typedef struct bbc_tuning {
     int32_t dense_min_permille;/* reserved for a block-level hash path (unused) */
     int32_t split_wedges;      /* anchors with more wedges than this are split into
                                   tile-range items that run on different blocks; an
-                                  anchor heavier than split_wedges / 2 times its tiles
-                                  also has each tile's centres cut into parts (up to 64, of
+                                  anchor that wants more such items than half its tiles
+                                  also has each tile's centres cut into parts (2 to 64, of
                                   about split_wedges / 16 wedges) whose counts are merged
                                   in device memory (at most the larger of 8 bytes per
                                   edge and 16 MiB, else no centre split) */

@@ -305,8 +305,9 @@ __device__ __forceinline__ void classify_one(const ClassifyParams &P, const int6
     long long g = 1;
     if ((long long)wl > P.split) g = ((long long)wl + P.split - 1) / P.split;
     if (P.centre_split && count_tiles && 2 * g > nt) {
-        // more wedges than nt tile ranges of half a `split` each: cut every tile's
-        // centres too
+        // the tile ranges it wants (ceil(wl / split)) are more than half its tiles: cut
+        // every tile's centres too, into parts of about split / kCentreSplitDiv wedges
+        // (an anchor too light for two parts stays whole)
         const long long per_part = P.split / kCentreSplitDiv > 0 ? P.split / kCentreSplitDiv : 1;
         long long k = ((long long)wl + (long long)nt * per_part - 1) / ((long long)nt * per_part);
         if (k > kMaxParts) k = kMaxParts;
