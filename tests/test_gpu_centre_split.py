@@ -2,7 +2,8 @@
 over the blocks have each tile's centres cut into parts whose counts are merged in global
 memory. Small split thresholds force the split on small graphs; totals and every
 per-vertex count must equal the oracle's, for 8-, 16- and 32-bit counter tiles, one and
-several tiles per anchor, both orientations, repeated counts and batches.
+several tiles per anchor, repeated counts and batches (and, under the same small split,
+the low-anchor orientation, whose light anchors stay whole).
 """
 
 from __future__ import annotations
