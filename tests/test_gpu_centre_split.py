@@ -24,7 +24,7 @@ def _tuning(**kw):
     return t
 
 
-def _hub_graph(seed=1):
+def _hub_graph(seed=1, hubs=10, d_lo=3_000, d_hi=12_000):
     """20,000 pair-side (U) vertices over 30,000 centres: ten hubs of 3,000 to 12,000
     centres (pairs of hubs share hundreds: 16-bit counters), 200 vertices of 300 centres
     and the rest of 5, so that a hub's endpoint range holds a 16-bit tile and an 8-bit
@@ -32,13 +32,13 @@ def _hub_graph(seed=1):
     rng = np.random.default_rng(seed)
     n_u, n_v = 20_000, 30_000
     us, vs = [], []
-    for x, d in enumerate(np.linspace(3_000, 12_000, 10).astype(int)):
+    for x, d in enumerate(np.linspace(d_lo, d_hi, hubs).astype(int)):
         us.append(np.full(d, x))
         vs.append(rng.choice(n_v, size=d, replace=False))
-    for x in range(10, 210):
+    for x in range(hubs, hubs + 200):
         us.append(np.full(300, x))
         vs.append(rng.choice(n_v, size=300, replace=False))
-    rest = np.arange(210, n_u)
+    rest = np.arange(hubs + 200, n_u)
     us.append(np.repeat(rest, 5))
     vs.append(rng.integers(0, n_v, size=5 * rest.size))
     key = np.unique(np.concatenate(us) * n_v + np.concatenate(vs))
@@ -137,3 +137,18 @@ def test_batch_with_split_members(gpu_lib):
     finally:
         for h in G:
             h.free()
+
+
+def test_serving_parts_across_ticks(gpu_lib):
+    """The serving loop takes a bounded number of a request's tile items per tick, so parts
+    of one centre-split tile can run in different launches; the merged counters are cleared
+    once per request and the last part, in whichever tick, completes the tile."""
+    gs = [_hub_graph(seed=7, hubs=60, d_lo=2_048, d_hi=8_000), _hub_graph(seed=8, hubs=60, d_lo=2_048, d_hi=8_000)]
+    want = [oracle.count(g, threads=8, per_vertex=False).balanced for g in gs]
+    srv = bbc.Server(4 << 30, tuning=_tuning(split_wedges=20_000, tile_words=4096, blocks_per_sm=1))
+    try:
+        tickets = [srv.submit(g) for g in gs]
+        assert [srv.wait(t, timeout_s=120.0) for t in tickets] == want
+        assert max(srv.request_info(t)["ticks"] for t in tickets) >= 2
+    finally:
+        srv.close()
